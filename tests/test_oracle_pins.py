@@ -1,0 +1,375 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each checks a value printed in the
+paper, a closed form derived by hand from Eq. 7, an identity that the reproducing
+construction (Eq. 2-3, 15-16) guarantees, or the paper's stated convergence rate.
+A dropped term, a wrong sign or index, or a transposed operand in the oracle fails
+at least one of them (noted per test).
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from oracle.oracle import Oracle, apply_K_sampled, b_sampled, phi1
+from paper_2403_19854_gb300 import workloads as W
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def _cube(nb, a, deg=1, kind="sin"):
+    lohi = (-1.0, 1.0) if kind == "paper" else (0.0, 1.0)
+    return W.cube_problem(nb, a, deg, kind, *lohi)
+
+
+def _coords(p):
+    X, Y, Z = p.coords()
+    return np.stack([X, Y, Z], 1)
+
+
+# --------------------------------------------------------------------------- Eq. 7
+def test_kernel_values_eq7():
+    """phi at hand-evaluated points of Eq. 7 (golden), both branches, the support end."""
+    for z, num, den in read_golden("phi_eq7.txt"):
+        assert phi1(float(z)) == pytest.approx(int(num) / int(den), abs=1e-15)
+        assert phi1(-float(z)) == phi1(float(z))
+
+
+def test_kernel_c2_continuity_eq7():
+    """Eq. 7 is a cubic B-spline: value, slope and curvature continuous at z = 1/2, and
+    it reaches 0 with zero slope at z = 1 (a wrong coefficient breaks one of these)."""
+    e = 1e-5
+    for z0 in (0.5, 1.0):
+        left = [phi1(z0 - k * e) for k in (0, 1, 2)]
+        right = [phi1(z0 + k * e) for k in (0, 1, 2)] if z0 < 1 else [0.0, 0.0, 0.0]
+        dl = (left[0] - left[1]) / e
+        dr = (right[1] - right[0]) / e if z0 < 1 else 0.0
+        assert abs(dl - dr) < 1e-4
+    # curvature at 1/2: 4 from both sides (second differences)
+    c_left = (phi1(0.5) - 2 * phi1(0.5 - 1e-3) + phi1(0.5 - 2e-3)) / 1e-6
+    c_right = (phi1(0.5) - 2 * phi1(0.5 + 1e-3) + phi1(0.5 + 2e-3)) / 1e-6
+    assert abs(c_left - c_right) < 0.05
+
+
+def test_bspline_partition_of_unity_at_a2():
+    """With a = 2h the profile is the uniform cubic B-spline, whose integer shifts sum
+    to one at every point: sum_i phi(|u - i| / 2) = 1."""
+    for u in np.linspace(0.0, 1.0, 11):
+        s = sum(phi1(abs(u - i) / 2.0) for i in range(-3, 5))
+        assert s == pytest.approx(1.0, abs=1e-15)
+
+
+# ------------------------------------------------------------------ Sec. 5.1, Tab.
+def test_box_rule_tab1_tab10():
+    """Domain nodes per box side match Tab. 1 (a = 1.5h) and Tab. 10 (a = 3.5h)."""
+    for side, a, total in read_golden("tab1_tab10_box_nodes.txt"):
+        assert W.domain_side(int(side), float(a)) ** 3 == int(total)
+
+
+def test_neighbour_counts_tab4_tab5():
+    """Interior neighbour count M of Tab. 4-5 from the oracle's grid search."""
+    for a, M in read_golden("tab4_tab5_neighbours.txt"):
+        a = float(a)
+        p = _cube(14, a)
+        o = Oracle(p.n, p.h, a, 1, p.chi)
+        nb = o.node_box()
+        c = 4 + 14 * (4 + 14 * 4)
+        assert o.neighbour_count(int(np.searchsorted(nb, c))) == int(M)
+
+
+def test_neighbour_search_equals_brute_force():
+    """Grid search over +-reach == O(N^2) scan over all nodes, on an irregular domain."""
+    p = W.spheres_problem(n_box=12, n_spheres=3, a_tilde=2.5, degree=1, r_range=(0.15, 0.3), seed=7)
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    for S in range(0, o.nnode, max(1, o.nnode // 97)):
+        assert o.neighbour_count(S) == o.neighbour_count(S, brute_force=True)
+
+
+# ----------------------------------------------------------- reproducing conditions
+def _monomials(deg):
+    out = [(0, 0, 0)]
+    out += [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    if deg == 2:
+        out += [(2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 0, 2)]
+    return out
+
+
+@pytest.mark.parametrize("case", ["cube1", "cube2", "spheres1", "spheres2"])
+def test_reproducing_conditions(case):
+    """sum_I Psi_I(x_S) (x_I - x_S)^alpha = delta_{alpha,0} and
+    sum_I Psi^{grad k}_I(x_S) (x_I - x_S)^alpha = delta_{alpha,e_k} for |alpha| <= n at every
+    node (Eq. 2-3 and 15-16).  A wrong row of M^{-1}, a wrong basis entry or a sign
+    error in Eq. 46-47 fails this."""
+    deg = 1 if case.endswith("1") else 2
+    a = 2.5 if deg == 1 else 3.0
+    if case.startswith("cube"):
+        p = _cube(12, a, deg)
+    else:
+        p = W.spheres_problem(n_box=16, n_spheres=3, a_tilde=a, degree=deg, r_range=(0.2, 0.3), seed=11)
+    o = Oracle(p.n, p.h, a, deg, p.chi)
+    assert o.nsingular == 0
+    nbr, psi, dpsi = o.shape_tables()
+    nb = o.node_box()
+    X = _coords(p)
+    xs = X[nb]
+    valid = nbr >= 0
+    xI = X[nb[np.where(valid, nbr, 0)]]
+    rel = (xI - xs[:, None, :]) / (a * np.asarray(p.h))  # scaled offsets, O(1)
+    hh = np.asarray(p.h)
+    for al in _monomials(deg):
+        mono = np.where(valid, rel[..., 0] ** al[0] * rel[..., 1] ** al[1] * rel[..., 2] ** al[2], 0.0)
+        target = 1.0 if al == (0, 0, 0) else 0.0
+        assert np.abs((psi * mono).sum(1) - target).max() < 1e-12
+        for k in range(3):
+            ek = tuple(1 if j == k else 0 for j in range(3))
+            # Psi^grad has units 1/length; with scaled offsets the identity reads
+            # sum Psi^grad_k * rel^alpha * a = delta_{alpha, e_k}
+            t = 1.0 if al == ek else 0.0
+            got = (dpsi[..., k] * mono).sum(1) * a * hh[k]
+            assert np.abs(got - t).max() < 1e-11
+
+
+# ------------------------------------------------------ closed-form interior stencil
+def _w_a2():
+    return {-1: Fraction(1, 6), 0: Fraction(2, 3), 1: Fraction(1, 6)}
+
+
+def test_interior_shape_functions_closed_form_a2():
+    """At a = 2h the interior moment matrix is diag(1, 1/12, 1/12, 1/12) (scaled basis):
+    Psi_I(x_S) = w w w and Psi^{grad x}_I(x_S) = o_x/(2h) w(o_y) w(o_z) with the B-spline
+    weights w = (1/6, 2/3, 1/6), i.e. a central difference smoothed by the B-spline."""
+    p = _cube(14, 2.0)
+    o = Oracle(p.n, p.h, 2.0, 1, p.chi)
+    nbr, psi, dpsi = o.shape_tables()
+    nb = o.node_box()
+    h = p.h[0]
+    w = _w_a2()
+    S = int(np.searchsorted(nb, 5 + 14 * (6 + 14 * 5)))
+    for sl in range(27):
+        ox, oy, oz = sl % 3 - 1, (sl // 3) % 3 - 1, sl // 9 - 1
+        assert psi[S, sl] == pytest.approx(float(w[ox] * w[oy] * w[oz]), abs=1e-15)
+        assert dpsi[S, sl, 0] * 2 * h == pytest.approx(float(ox * w[oy] * w[oz]), abs=1e-14)
+        assert dpsi[S, sl, 1] * 2 * h == pytest.approx(float(oy * w[ox] * w[oz]), abs=1e-14)
+        assert dpsi[S, sl, 2] * 2 * h == pytest.approx(float(oz * w[ox] * w[oy]), abs=1e-14)
+    bf = o.b_fields()
+    c = 5 + 14 * (6 + 14 * 5)
+    assert bf[0, :, c] == pytest.approx([1, 0, 0, 0], abs=1e-14)
+    assert bf[1, :, c] * h == pytest.approx([0, -6, 0, 0], abs=1e-12)   # -(1/a) * 12, a = 2h
+
+
+def test_interior_stiffness_row_closed_form_a2():
+    """Deep-interior rows of K at a = 2h equal h^3 sum_k D_k^T D_k with the exact
+    rational stencil above (K_{I,I+D} = (h/4) * integer/1296), computed with fractions.
+    Pins V, the DNI sum of Eq. 54 and the pairing of I and J."""
+    p = _cube(14, 2.0)
+    o = Oracle(p.n, p.h, 2.0, 1, p.chi)
+    o.assemble_K(p.V)
+    ptr, col, val = o.K_csr()
+    nb = o.node_box()
+    h = p.h[0]
+    w = _w_a2()
+    offs = [(x, y, z) for z in (-1, 0, 1) for y in (-1, 0, 1) for x in (-1, 0, 1)]
+
+    def c(k, o3):
+        others = [w[o3[j]] for j in range(3) if j != k]
+        return o3[k] * others[0] * others[1]
+
+    exact = {}
+    for D in [(x, y, z) for z in range(-2, 3) for y in range(-2, 3) for x in range(-2, 3)]:
+        s = Fraction(0)
+        for o3 in offs:
+            o2 = (o3[0] + D[0], o3[1] + D[1], o3[2] + D[2])
+            if max(abs(v) for v in o2) > 1:
+                continue
+            for k in range(3):
+                s += c(k, o3) * c(k, o2)
+        exact[D] = s
+    n = 14
+    for (i, j, k) in [(5, 6, 5), (2, 2, 2), (6, 4, 7)]:
+        I = int(np.searchsorted(nb, i + n * (j + n * k)))
+        row = {}
+        for e in range(ptr[I], ptr[I + 1]):
+            J = nb[col[e]]
+            D = (J % n - i, (J // n) % n - j, J // (n * n) - k)
+            row[D] = val[e]
+        for D, v in exact.items():
+            assert row.get(D, 0.0) == pytest.approx(float(v) * h / 4.0, rel=1e-12, abs=1e-15 * h)
+
+
+def test_interior_gradient_stencil_a25_properties():
+    """At a = 2.5h (reach 2) the interior implicit gradient is antisymmetric in the
+    derivative axis, exact on linear functions (sum_o c(o) o_x h = 1), and proportional
+    to o_x phi(|o_x|/2.5) along that axis (the diagonal moment matrix of the interior)."""
+    p = _cube(14, 2.5)
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    nbr, psi, dpsi = o.shape_tables()
+    nb = o.node_box()
+    h = p.h[0]
+    S = int(np.searchsorted(nb, 5 + 14 * (5 + 14 * 5)))
+    g = dpsi[S, :, 0].reshape(5, 5, 5)  # [oz, oy, ox]
+    assert np.abs(g + g[:, :, ::-1]).max() < 1e-13 / h
+    ox = np.arange(-2, 3)
+    assert (g.sum(axis=(0, 1)) * ox * h).sum() == pytest.approx(1.0, abs=1e-13)
+    prof = g.sum(axis=(0, 1))
+    ratio = prof[3] / prof[4]
+    assert ratio == pytest.approx((1 * phi1(1 / 2.5)) / (2 * phi1(2 / 2.5)), rel=1e-12)
+
+
+# ------------------------------------------------------------------ stiffness matrix
+@pytest.mark.parametrize("deg,a,geom", [(1, 2.0, "cube"), (1, 2.5, "spheres"), (2, 3.0, "cube")])
+def test_stiffness_symmetric_psd_constants_in_null_space(deg, a, geom):
+    """K of Eq. 26 is symmetric, positive semidefinite, and K.1 = 0 before boundary
+    conditions (the implicit gradient reproduces constants with zero gradient)."""
+    if geom == "cube":
+        p = _cube(10 if deg == 1 else 12, a, deg)
+    else:
+        p = W.spheres_problem(n_box=14, n_spheres=2, a_tilde=a, degree=deg, r_range=(0.25, 0.3), seed=5)
+    o = Oracle(p.n, p.h, a, deg, p.chi)
+    o.assemble_K(p.V)
+    ptr, col, val = o.K_csr()
+    K = np.zeros((o.nnode, o.nnode))
+    for I in range(o.nnode):
+        K[I, col[ptr[I]:ptr[I + 1]]] = val[ptr[I]:ptr[I + 1]]
+    nrm = np.abs(K).max()
+    assert np.abs(K - K.T).max() <= 1e-14 * nrm
+    assert np.abs(K.sum(1)).max() <= 1e-13 * nrm
+    assert np.linalg.eigvalsh(K).min() >= -1e-12 * nrm
+
+
+def test_energy_of_linear_field_equals_volume():
+    """For d = a.x + c the implicit gradient is exactly a at every node, so
+    d^T K d = |a|^2 sum_S V_S = |a|^2 (unit cube, trapezoidal V sums to 1).
+    A wrong V, a dropped gradient component or a missing DNI weight fails this."""
+    for a_t, deg in ((2.0, 1), (2.5, 1), (3.0, 2)):
+        p = _cube(12, a_t, deg)
+        o = Oracle(p.n, p.h, a_t, deg, p.chi)
+        X = _coords(p)
+        av = np.array([0.3, -1.2, 0.7])
+        d = np.where(p.chi > 0, X @ av + 0.4, 0.0)
+        f = o.apply_K(p.V, d)
+        assert p.V.sum() == pytest.approx(1.0, abs=1e-14)
+        assert float(d @ f) == pytest.approx(float(av @ av), rel=1e-12)
+
+
+def test_matrix_free_equals_assembled():
+    """Matrix-free neighbour loops (g = B d, f = B^T V g) == assembled CSR SpMV."""
+    p = W.spheres_problem(n_box=14, n_spheres=3, a_tilde=2.5, degree=1, r_range=(0.2, 0.3), seed=3)
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    d = W.random_field(p.nbox, 1) * p.chi
+    f1 = o.apply_K(p.V, d)
+    o.assemble_K(p.V)
+    f2 = o.spmv(d)
+    assert np.abs(f1 - f2).max() <= 1e-13 * np.abs(f1).max()
+
+
+def test_sampled_mode_equals_tables():
+    """Per-node recomputation (used at full sizes) == the tabulated discretisation."""
+    p = W.spheres_problem(n_box=14, n_spheres=3, a_tilde=3.0, degree=2, r_range=(0.15, 0.25), seed=9)
+    o = Oracle(p.n, p.h, 3.0, 2, p.chi)
+    d = W.random_field(p.nbox, 2) * p.chi
+    f = o.apply_K(p.V, d)
+    sample = np.flatnonzero(p.chi)[::7]
+    fs = apply_K_sampled(p.n, p.h, 3.0, 2, p.chi, p.V, d, sample)
+    assert np.abs(fs - f[sample]).max() <= 1e-13 * np.abs(f).max()
+    bs = b_sampled(p.n, p.h, 3.0, 2, p.chi, sample)
+    bf = o.b_fields()
+    assert np.abs(bs - np.transpose(bf[:, :, sample], (2, 0, 1))).max() <= 1e-12 * np.abs(bf).max()
+
+
+# ---------------------------------------------------------------- f^r and u^h
+def test_rhs_moments():
+    """sum_I f^r_I x_I^alpha = sum_S V_S r_S x_S^alpha for |alpha| <= n (Eq. 59 with the
+    reproducing condition).  Transposing Psi_I(x_S) into Psi_S(x_I) breaks it."""
+    p = W.spheres_problem(n_box=16, n_spheres=3, a_tilde=2.5, degree=1, r_range=(0.2, 0.3), seed=4)
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    r = W.random_field(p.nbox, 5) * p.chi
+    fr = o.rhs(p.V, r)
+    X = _coords(p)
+    for al in _monomials(1):
+        mono = X[:, 0] ** al[0] * X[:, 1] ** al[1] * X[:, 2] ** al[2]
+        lhs = float(fr @ mono)
+        rhs = float((p.V * r * p.chi) @ mono)
+        assert lhs == pytest.approx(rhs, rel=1e-12, abs=1e-15)
+
+
+@pytest.mark.parametrize("deg,a", [(1, 2.5), (2, 3.0)])
+def test_eval_u_reproduces_polynomials(deg, a):
+    """u^h of Eq. 62 with d = a polynomial of degree <= n returns that polynomial at every
+    node (near boundaries too)."""
+    p = W.spheres_problem(n_box=16, n_spheres=3, a_tilde=a, degree=deg, r_range=(0.2, 0.3), seed=6)
+    o = Oracle(p.n, p.h, a, deg, p.chi)
+    X = _coords(p)
+    q = 0.2 + 0.5 * X[:, 0] - 0.3 * X[:, 1] + 0.9 * X[:, 2]
+    if deg == 2:
+        q = q + 0.7 * X[:, 0] * X[:, 1] - 0.4 * X[:, 2] ** 2
+    d = np.where(p.chi > 0, q, 0.0)
+    u = o.eval_u(d)
+    m = p.chi > 0
+    assert np.abs(u[m] - q[m]).max() < 1e-12
+
+
+# ---------------------------------------------------------------- solve
+def test_solve_satisfies_dirichlet_system():
+    """d = g on Gamma_g (Eq. 29) and K_OO d_O = f^r_O - K_OG g_G on the free nodes."""
+    p = _cube(10, 2.0)
+    p.g = np.where(p.chi_gamma > 0, W.random_field(p.nbox, 8), 0.0)
+    o = Oracle(p.n, p.h, 2.0, 1, p.chi)
+    d, info = o.solve(p.V, p.chi_gamma, p.r, p.g)
+    gam = p.chi_gamma > 0
+    free = (p.chi > 0) & ~gam
+    assert np.array_equal(d[gam], p.g[gam])
+    res = o.spmv(d) - o.rhs(p.V, p.r)
+    assert np.abs(res[free]).max() <= 1e-12 * np.abs(o.rhs(p.V, p.r)).max()
+
+
+@pytest.mark.slow
+def test_manufactured_solution_quadratic_rate_paper_3d():
+    """The 3D problem of Sec. 6.1.3 (Eq. 106-108: a = 1.5h, linear basis, u = prod(1-x_k^2)
+    on [-1,1]^3) converges at the quadratic rate the paper states for RKPM with n = 1
+    (Sec. 6.1.1-6.1.2; the 3D plot is Fig. 13).  Nodal normalised L2 error of Eq. 104."""
+    errs, hs = [], []
+    for nb in (12, 16, 24, 32):
+        p = _cube(nb, 1.5, 1, "paper")
+        o = Oracle(p.n, p.h, 1.5, 1, p.chi)
+        d, info = o.solve(p.V, p.chi_gamma, p.r, p.g, tol=1e-13)
+        assert info["converged"]
+        u = o.eval_u(d)
+        m = p.chi > 0
+        errs.append(np.sqrt(((u - p.u_exact)[m] ** 2).sum() / (p.u_exact[m] ** 2).sum()))
+        hs.append(p.h[0])
+    rates = np.diff(np.log(errs)) / np.diff(np.log(hs))
+    assert rates[-1] > 1.8 and rates[-1] < 2.3
+    assert np.polyfit(np.log(hs), np.log(errs), 1)[0] > 1.8
+
+
+def test_adjoint_gradient_matches_central_differences():
+    """J(r, g) = 1/2 |u^h - u_t|^2 is quadratic in (r, g), so central differences are exact
+    up to rounding; the oracle's adjoint gradient (assembled K) must match on seeded
+    directions."""
+    p = W.adjoint_problem(n_box=9, a_tilde=2.0, degree=1, seed=123, sigma=0.3)
+    o = Oracle(p.n, p.h, 2.0, 1, p.chi)
+    ut = p.meta["u_target"]
+    J, gr, gg, _, _ = o.adjoint(p.V, p.chi, p.chi_gamma, p.r, p.g, ut)
+    rng = np.random.default_rng(77)
+
+    def Jof(r, g):
+        d, _ = o.solve(p.V, p.chi_gamma, r, g)
+        e = np.where(p.chi > 0, o.eval_u(d) - ut, 0.0)
+        return 0.5 * float(e @ e)
+
+    for _ in range(4):
+        dr = rng.standard_normal(p.nbox) * p.chi
+        dg = rng.standard_normal(p.nbox) * p.chi_gamma
+        eps = 1e-2
+        fd = (Jof(p.r + eps * dr, p.g + eps * dg) - Jof(p.r - eps * dr, p.g - eps * dg)) / (2 * eps)
+        an = float(gr @ dr + gg @ dg)
+        assert an == pytest.approx(fd, rel=1e-9, abs=1e-12)
+
+
+def test_singular_moment_is_detected():
+    """A node with too few neighbours (an isolated node) has a singular M (Eq. 5 count)."""
+    chi = np.zeros(8 ** 3, dtype=np.uint8)
+    chi[3 + 8 * (3 + 8 * 3)] = 1
+    o = Oracle((8, 8, 8), (0.1, 0.1, 0.1), 2.0, 1, chi)
+    assert o.nsingular == 1 and o.first_singular == 3 + 8 * (3 + 8 * 3)
