@@ -1,0 +1,198 @@
+/*
+ * fcrkpm.h -- C ABI of the GB300 fast-convolving RKPM library (FC-RKPM,
+ * arXiv 2403.19854): the matrix-free Galerkin operator of the 3D Poisson problem
+ * (Eq. 8-9) written as circular convolutions on a periodic node box (Sec. 4),
+ * evaluated with FFTs on the GPU, and the conjugate-gradient solve around it
+ * (Alg. 5).
+ *
+ * Conventions shared by every entry point
+ *  - Grid: a periodic box of n[0] x n[1] x n[2] nodes with spacing h[k]
+ *    (Eq. 70), x fastest: a field is an array of n0*n1*n2 values indexed
+ *    i + n0*(j + n1*k).  n[0] must be even and n[1]*n[2] even; each n[k] must be
+ *    one of the FFT line lengths the library was built for (rk_supported_length).
+ *  - Domain: chi (Eq. 40) is 1 on the nodes of Omega and 0 on the gap; chi_gamma
+ *    (Eq. 95) is 1 on the nodes where d = g is imposed (Eq. 29), a subset of chi.
+ *    The gap must be at least l_e = (floor(a_tilde) + 1) h wide on every axis
+ *    (Eq. 66): a node of Omega may not see another node of Omega across the
+ *    periodic boundary within the support; rk_setup checks this.
+ *  - Basis: degree 1 (s = 4, H = [1, x, y, z]) or 2 (s = 10, H = [1, x, y, z,
+ *    x^2, xy, xz, y^2, yz, z^2]), Eq. 4-5, evaluated on the scaled offset
+ *    (x - x_I)/a (each monomial divided by a^|alpha|; Psi is unchanged).  Kernel:
+ *    tensor cubic B-spline of Eq. 6-7 with a_k = a_tilde * h[k] (Eq. 64).
+ *  - Pointers: every array argument may be a host pointer or a device pointer of
+ *    the current device (the library asks the CUDA driver which).  Device
+ *    arrays are used in place and must be aligned to 16 bytes; host arrays are
+ *    staged through library-owned device buffers and the call returns only after
+ *    the host output is written.  The caller owns all arrays it passes; the
+ *    handle owns everything it allocates.
+ *  - Streams: stream is a cudaStream_t (NULL = legacy default stream).  Work on
+ *    device arrays is stream-ordered; calls that report a convergence status
+ *    (rk_solve, rk_solve_adjoint) synchronise the stream before returning.
+ *  - Errors: no call aborts or prints.  Every call returns an rk_status;
+ *    rk_status_string() names it and rk_last_error_message() describes the last
+ *    failure of the calling thread.
+ *  - Thread safety: a handle may be used by one host thread at a time.
+ */
+#ifndef FCRKPM_H
+#define FCRKPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rk_status {
+  RK_OK = 0,
+  RK_ERR_INVALID_ARG = 1,      /* bad pointer, size, alignment or option */
+  RK_ERR_CUDA = 2,             /* a CUDA runtime call failed */
+  RK_ERR_OOM = 3,              /* device allocation failed */
+  RK_ERR_SINGULAR_MOMENT = 4,  /* M(x) not positive definite at some node of Omega */
+  RK_ERR_NOT_CONVERGED = 5,    /* iteration cap reached before the tolerance */
+  RK_ERR_BREAKDOWN = 6,        /* CG breakdown: p^T A p <= 0 or not finite */
+  RK_ERR_TIMEOUT = 7,          /* a bounded device-side wait ran out */
+  RK_ERR_UNSUPPORTED = 8       /* grid size not built, gap too narrow, odd n[0] ... */
+} rk_status;
+
+typedef enum rk_dtype { RK_F64 = 0, RK_F32 = 1 } rk_dtype;
+
+typedef enum rk_precision {
+  RK_PREC_FP64 = 0,  /* every convolution and CG vector in FP64 */
+  RK_PREC_MIXED = 1  /* FP32 convolutions and CG vectors, FP64 dots, FP64 refinement */
+} rk_precision;
+
+typedef struct rk_grid {
+  int32_t n[3]; /* box nodes per axis */
+  double h[3];  /* node spacing per axis */
+} rk_grid;
+
+typedef struct rk_handle rk_handle;
+
+typedef struct rk_solve_opts {
+  double tol;         /* stop when ||F - A d||_2 / ||F||_2 <= tol, FP64 residual (default 1e-10) */
+  int32_t max_iter;   /* cap on CG iterations, all refinement steps together (default 200000) */
+  int32_t precision;  /* rk_precision (default RK_PREC_MIXED) */
+  double inner_tol;   /* mixed: relative residual target of each FP32 inner solve (default 1e-4) */
+  int32_t max_outer;  /* mixed: cap on refinement steps (default 60) */
+  int32_t check_every;/* iterations between host-side convergence checks (default 25) */
+  int32_t x0_given;   /* 1: on entry d holds an initial guess on the free nodes */
+  int32_t reserved;
+} rk_solve_opts;
+
+typedef struct rk_solve_info {
+  int32_t iterations;   /* CG iterations (inner iterations in mixed mode) */
+  int32_t outer;        /* refinement steps (mixed) */
+  int32_t matvec_f32;   /* FP32 K.u applications */
+  int32_t matvec_f64;   /* FP64 K.u applications */
+  double rel_residual;  /* final ||F - A d|| / ||F|| in FP64 */
+  double f_norm;        /* ||F||, F = chi_Omega (f^r - K d_Gamma) */
+  double setup_ms;      /* unused by rk_solve (0) */
+  double solve_ms;      /* wall time of the call on the stream */
+  int32_t status;       /* rk_status of the solve */
+  int32_t reserved;
+} rk_solve_info;
+
+/* Default options (tol 1e-10, mixed precision). */
+void rk_default_solve_opts(rk_solve_opts* opts);
+
+/* 1 if the library holds FFT kernels for a box side of n nodes, else 0. */
+int rk_supported_length(int n);
+
+/*
+ * rk_setup -- Alg. 1 and the "Initialize" block of Alg. 5.
+ * Builds the per-axis kernel tables (the separable factors of H_p, H^a_p and
+ * their spectra, Eq. 72-79), the moment fields M_pq = (1 - chi) delta_pq +
+ * chi o F^-1[F(chi) o F(H_p o H^a_q)] (Eq. 80) in FP64, solves the s x s system
+ * at every node (FP64 Cholesky) and stores b^0, b^x, b^y, b^z (Eq. 83-85) in FP64
+ * and FP32, plus chi*V (Eq. 87).
+ *   grid       box size and spacing
+ *   chi        uint8[nbox], Eq. 40
+ *   chi_gamma  uint8[nbox], Eq. 95 (NULL: no Dirichlet nodes)
+ *   V          double[nbox], nodal volumes of direct nodal integration (Eq. 54, 87)
+ *   degree     1 or 2 (Eq. 4-5)
+ *   a_tilde    support in units of h (Eq. 64), 0.5 < a_tilde < 16
+ *   stream     cudaStream_t for the set-up work (synchronised before return)
+ *   out        receives the handle
+ * Errors: RK_ERR_INVALID_ARG, RK_ERR_UNSUPPORTED (size not built, odd sizes, gap
+ * narrower than Eq. 66), RK_ERR_OOM, RK_ERR_CUDA, RK_ERR_SINGULAR_MOMENT (the
+ * handle is still returned; rk_singular_nodes gives the count and first node).
+ */
+rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_gamma, const double* V,
+                   int32_t degree, double a_tilde, void* stream, rk_handle** out);
+
+/* Number of nodes of Omega whose moment matrix was singular, and the flat index
+ * of the first one (-1 if none). */
+rk_status rk_singular_nodes(const rk_handle* h, int64_t* count, int64_t* first);
+
+/*
+ * rk_apply_K -- Alg. 2: f^int = K d (Eq. 57, 91) with direct nodal integration.
+ *   d  [nbox] coefficients (values off chi are ignored: Eq. 91 uses chi o d)
+ *   f  [nbox] output, 0 off chi
+ *   dtype  RK_F64: double arrays, FP64 path;  RK_F32: float arrays, FP32 path
+ */
+rk_status rk_apply_K(rk_handle* h, const void* d, void* f, int32_t dtype, void* stream);
+
+/* rk_rhs -- Alg. 4 with the reflected kernel of Eq. 60/92:
+ * f^r = chi o F^-1[ sum_p F(chi o V o b^0_p o r) o F(Hbar^a_p) ].  r, fr: double[nbox]. */
+rk_status rk_rhs(rk_handle* h, const double* r, double* fr, void* stream);
+
+/* rk_eval_u -- Alg. 3: u^h = chi o sum_p b^0_p o F^-1[F(chi o d) o F(H^a_p)] (Eq. 63, 94).
+ * d, u: double[nbox]. */
+rk_status rk_eval_u(rk_handle* h, const double* d, double* u, void* stream);
+
+/* rk_eval_u_transpose -- transpose of Alg. 3 (the operator of Alg. 4 without V):
+ * w = chi o F^-1[ sum_p F(chi o b^0_p o e) o F(Hbar^a_p) ].  e, w: double[nbox]. */
+rk_status rk_eval_u_transpose(rk_handle* h, const double* e, double* w, void* stream);
+
+/* rk_get_b -- the correction coefficients of Eq. 83-85 (FP64, scaled basis):
+ * b[(i*s + p)*nbox + idx] for i = 0 (b^0), 1 (b^x), 2 (b^y), 3 (b^z). */
+rk_status rk_get_b(rk_handle* h, double* b, void* stream);
+
+/* Sizes of the handle: box nodes, s, and the number of nodes with chi = 1. */
+rk_status rk_get_shape(const rk_handle* h, int32_t n[3], int32_t* s, int64_t* n_omega);
+
+/*
+ * rk_solve -- Alg. 5 with strong Dirichlet conditions (Eq. 29, Sec. 5.4.2):
+ * d = g on chi_gamma; on the free nodes chi_Omega = chi - chi_gamma (Eq. 96)
+ * conjugate gradients solve chi_Omega o K(chi_Omega o x) = F with
+ * F = chi_Omega o (f^r - K d_Gamma) until ||F - A x|| <= tol ||F|| (FP64
+ * residual); then u^h = Alg. 3 (d).  In RK_PREC_MIXED the CG runs in FP32
+ * (FP32 convolutions and vectors, FP64 dot products) inside FP64 iterative
+ * refinement (FP64 residual with the FP64 operator).
+ *   r  [nbox] source (read on chi);  g  [nbox] Dirichlet data (read on chi_gamma)
+ *   d  [nbox] output coefficients (input guess if opts->x0_given);  u [nbox] output
+ *      u^h (NULL: not computed)
+ *   opts NULL: defaults;  info NULL: not reported
+ * Errors: RK_ERR_NOT_CONVERGED, RK_ERR_BREAKDOWN (outputs hold the last iterate),
+ * and the argument errors above.
+ */
+rk_status rk_solve(rk_handle* h, const double* r, const double* g, double* d, double* u,
+                   const rk_solve_opts* opts, rk_solve_info* info, void* stream);
+
+/*
+ * rk_solve_adjoint -- gradient of J = 1/2 sum_{chi} (u^h - u_target)^2 with respect
+ * to the source r and the Dirichlet data g, for the solve of rk_solve.  The forward
+ * solve is recomputed from (r, g) (nothing is kept between calls); one adjoint
+ * solve chi_Omega K chi_Omega lambda = chi_Omega U^T e with e = chi o (u^h - u_target)
+ * (K is symmetric) gives dJ/dr = chi V o U lambda and dJ/dg = chi_gamma o
+ * (U^T e - K lambda), U being Alg. 3 (derivation from Eq. 25, 29, 59, 62).
+ *   J (double, host) may be NULL;  dJ_dr, dJ_dg: [nbox] outputs.
+ */
+rk_status rk_solve_adjoint(rk_handle* h, const double* r, const double* g, const double* u_target,
+                           double* dJ_dr, double* dJ_dg, double* J, const rk_solve_opts* opts,
+                           rk_solve_info* info, void* stream);
+
+/* Release the handle and everything it owns (NULL is accepted). */
+rk_status rk_destroy(rk_handle* h);
+
+/* Static string naming a status code. */
+const char* rk_status_string(rk_status s);
+
+/* Description of the last error raised on the calling host thread ("" if none). */
+const char* rk_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCRKPM_H */

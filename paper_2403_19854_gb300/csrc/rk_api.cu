@@ -1,0 +1,1103 @@
+// rk_api.cu -- host side of the FC-RKPM library: the C ABI declared in
+// include/fcrkpm.h.  Owns the handle (tables, coefficient fields, workspaces),
+// sequences the axis passes into the operators of Alg. 1-4 and runs the
+// conjugate-gradient driver of Alg. 5 (plain FP64, or FP32 inner solves inside
+// FP64 iterative refinement).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fcrkpm.h"
+#include "rk_internal.cuh"
+
+using namespace rk;
+
+namespace {
+
+thread_local std::string g_err;
+
+rk_status fail(rk_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+rk_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? RK_ERR_OOM : RK_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RK_CK(...)                                               \
+  do {                                                           \
+    cudaError_t e_ = (__VA_ARGS__);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #__VA_ARGS__);   \
+  } while (0)
+
+#define RK_TRY(call)                     \
+  do {                                   \
+    rk_status s_ = (call);               \
+    if (s_ != RK_OK) return s_;          \
+  } while (0)
+
+// Eq. 7 with z >= 1 -> 0; second branch in the factored form (4/3)(1 - z)^3.
+double kernel_profile(double z) {
+  z = std::fabs(z);
+  if (z >= 1.0) return 0.0;
+  if (z <= 0.5) return 2.0 / 3.0 - 4.0 * z * z + 4.0 * z * z * z;
+  const double t = 1.0 - z;
+  return (4.0 / 3.0) * t * t * t;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Monomial exponents of the basis (Eq. 4 in 3D), graded order.
+void basis_exponents(int degree, int alpha[][3]) {
+  static const int e[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                               {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
+  const int s = degree == 1 ? 4 : 10;
+  for (int p = 0; p < s; ++p)
+    for (int k = 0; k < 3; ++k) alpha[p][k] = e[p][k];
+}
+
+// Structure of the forward / reflected chains for the basis of the handle:
+// x-pass outputs m_x in [0, deg]; y-pass outputs = groups (m_x, m_y); z terms (m_z, p).
+struct Chain {
+  int deg = 1, s = 4;
+  int alpha[10][3];
+  int nX = 0;
+  int nY = 0;
+  int ymx[kMaxIn], ymy[kMaxIn];
+  std::vector<std::pair<int, int>> zterms[kMaxIn];  // (m_z, p)
+  void build(int degree) {
+    deg = degree;
+    s = degree == 1 ? 4 : 10;
+    basis_exponents(degree, alpha);
+    nX = deg + 1;
+    nY = 0;
+    for (int p = 0; p < s; ++p) {
+      int g = -1;
+      for (int q = 0; q < nY; ++q)
+        if (ymx[q] == alpha[p][0] && ymy[q] == alpha[p][1]) g = q;
+      if (g < 0) {
+        g = nY++;
+        ymx[g] = alpha[p][0];
+        ymy[g] = alpha[p][1];
+        zterms[g].clear();
+      }
+      zterms[g].push_back({alpha[p][2], p});
+    }
+  }
+};
+
+}  // namespace
+
+// --------------------------------------------------------------------- handle
+struct rk_handle {
+  int n[3];
+  double h[3];
+  double a_tilde;
+  int degree, s;
+  int reach;
+  long long nbox;
+  long long n_omega;
+  int device;
+  Chain chain;
+  // inputs and coefficient fields (device)
+  uint8_t* chi = nullptr;
+  uint8_t* chi_gamma = nullptr;
+  uint8_t* chi_omega = nullptr;
+  double* V = nullptr;
+  double* chiV64 = nullptr;
+  float* chiV32 = nullptr;
+  double* b64 = nullptr;  // [4][s][nbox]
+  float* b32 = nullptr;
+  // per-axis tables (device): spectral multipliers [2deg+1][n] and twiddles [n]
+  double* coef64[3] = {nullptr, nullptr, nullptr};
+  float* coef32[3] = {nullptr, nullptr, nullptr};
+  cpx<double>* tw64[3] = {nullptr, nullptr, nullptr};
+  cpx<float>* tw32[3] = {nullptr, nullptr, nullptr};
+  // workspaces of the operator chains: X outputs, Y outputs, z-pass outputs
+  double* ws64 = nullptr;
+  float* ws32 = nullptr;
+  // solver vectors (allocated on first solve)
+  double* sv64 = nullptr;  // x, r, p, Ap, F, d0, t0, t1
+  float* sv32 = nullptr;   // x, r, p, Ap
+  double* partials = nullptr;
+  double* dscal = nullptr;   // scratch scalars (device)
+  CGState* cg = nullptr;     // device CG state
+  double* hscal = nullptr;   // pinned host scalars
+  // staging of host arrays
+  double* stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  unsigned long long* counters = nullptr;  // singular count, first singular
+  long long n_singular = 0, first_singular = -1;
+  std::vector<void*> owned;
+
+  template <typename T>
+  rk_status alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    owned.push_back(q);
+    *p = (T*)q;
+    return RK_OK;
+  }
+  double* v64(int i) { return sv64 + (size_t)i * nbox; }
+  float* v32(int i) { return sv32 + (size_t)i * nbox; }
+  template <typename T>
+  T* ws(int i);
+};
+template <>
+double* rk_handle::ws<double>(int i) { return ws64 + (size_t)i * nbox; }
+template <>
+float* rk_handle::ws<float>(int i) { return ws32 + (size_t)i * nbox; }
+
+namespace {
+
+template <typename T>
+const T* coef_of(const rk_handle* h, int axis);
+template <>
+const double* coef_of<double>(const rk_handle* h, int axis) { return h->coef64[axis]; }
+template <>
+const float* coef_of<float>(const rk_handle* h, int axis) { return h->coef32[axis]; }
+template <typename T>
+const cpx<T>* tw_of(const rk_handle* h, int axis);
+template <>
+const cpx<double>* tw_of<double>(const rk_handle* h, int axis) { return h->tw64[axis]; }
+template <>
+const cpx<float>* tw_of<float>(const rk_handle* h, int axis) { return h->tw32[axis]; }
+template <typename T>
+const T* bfields(const rk_handle* h);
+template <>
+const double* bfields<double>(const rk_handle* h) { return h->b64; }
+template <>
+const float* bfields<float>(const rk_handle* h) { return h->b32; }
+template <typename T>
+const T* chiV(const rk_handle* h);
+template <>
+const double* chiV<double>(const rk_handle* h) { return h->chiV64; }
+template <>
+const float* chiV<float>(const rk_handle* h) { return h->chiV32; }
+
+template <typename T>
+PassArgs<T> pass_base(const rk_handle* h, int axis) {
+  PassArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.coef = coef_of<T>(h, axis);
+  a.tw = tw_of<T>(h, axis);
+  a.nx = h->n[0];
+  a.ny = h->n[1];
+  a.nz = h->n[2];
+  if (axis == 1) {
+    a.line_stride = h->n[0];
+    a.other_stride = (long long)h->n[0] * h->n[1];
+  } else if (axis == 2) {
+    a.line_stride = (long long)h->n[0] * h->n[1];
+    a.other_stride = h->n[0];
+  }
+  return a;
+}
+
+template <typename T>
+rk_status run_split(const rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s) {
+  cudaError_t e = launch_split<T>(axis, h->n[axis], a, s);
+  return e == cudaSuccess ? RK_OK : cuda_fail(e, "split pass");
+}
+template <typename T>
+rk_status run_merge(const rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s) {
+  cudaError_t e = launch_merge<T>(axis, h->n[axis], a, s);
+  return e == cudaSuccess ? RK_OK : cuda_fail(e, "merge pass");
+}
+
+// Workspace layout of the operator chains: [0, nX) x-pass outputs, [nX, nX+nY)
+// y-pass outputs, [nX+nY, nX+2nY) z-pass outputs.
+inline int ws_fields(const Chain& c) { return c.nX + 2 * c.nY; }
+
+// forward chain, x and y passes: E_{mx,my} = conv_x conv_y (mask o d)   (Alg. 2 line 1-2)
+template <typename T>
+rk_status chain_forward_xy(rk_handle* h, const T* d, const uint8_t* in_mask, cudaStream_t s) {
+  const Chain& c = h->chain;
+  PassArgs<T> ax = pass_base<T>(h, 0);
+  ax.in[0] = d;
+  ax.in_mask = in_mask;
+  ax.n_groups = 1;
+  ax.g_io[0] = 0;
+  ax.g_begin[0] = 0;
+  for (int m = 0; m < c.nX; ++m) {
+    ax.out[m] = h->ws<T>(m);
+    ax.term_io[m] = m;
+    ax.term_m[m] = m;
+  }
+  ax.g_begin[1] = c.nX;
+  RK_TRY(run_split<T>(h, 0, ax, s));
+  PassArgs<T> ay = pass_base<T>(h, 1);
+  ay.n_groups = c.nX;
+  int q = 0;
+  for (int mx = 0; mx < c.nX; ++mx) {
+    ay.in[mx] = h->ws<T>(mx);
+    ay.g_io[mx] = mx;
+    ay.g_begin[mx] = q;
+    for (int g = 0; g < c.nY; ++g)
+      if (c.ymx[g] == mx) {
+        ay.out[g] = h->ws<T>(c.nX + g);
+        ay.term_io[q] = g;
+        ay.term_m[q] = c.ymy[g];
+        ++q;
+      }
+  }
+  ay.g_begin[c.nX] = q;
+  return run_split<T>(h, 1, ay, s);
+}
+
+// reflected chain, y and x passes: f = out_mask o sum conv_x(Hbar) conv_y(Hbar) G   (Alg. 2 last line)
+template <typename T>
+rk_status chain_reflect_yx(rk_handle* h, T* f, const uint8_t* out_mask, cudaStream_t s) {
+  const Chain& c = h->chain;
+  PassArgs<T> ay = pass_base<T>(h, 1);
+  ay.reflect = 1;
+  ay.n_groups = c.nX;
+  int q = 0;
+  for (int mx = 0; mx < c.nX; ++mx) {
+    ay.out[mx] = h->ws<T>(mx);
+    ay.g_io[mx] = mx;
+    ay.g_begin[mx] = q;
+    for (int g = 0; g < c.nY; ++g)
+      if (c.ymx[g] == mx) {
+        ay.in[g] = h->ws<T>(c.nX + c.nY + g);
+        ay.term_io[q] = g;
+        ay.term_m[q] = c.ymy[g];
+        ++q;
+      }
+  }
+  ay.g_begin[c.nX] = q;
+  RK_TRY(run_merge<T>(h, 1, ay, s));
+  PassArgs<T> ax = pass_base<T>(h, 0);
+  ax.reflect = 1;
+  ax.out_mask = out_mask;
+  ax.n_groups = 1;
+  ax.out[0] = f;
+  ax.g_io[0] = 0;
+  ax.g_begin[0] = 0;
+  for (int m = 0; m < c.nX; ++m) {
+    ax.in[m] = h->ws<T>(m);
+    ax.term_io[m] = m;
+    ax.term_m[m] = m;
+  }
+  ax.g_begin[1] = c.nX;
+  return run_merge<T>(h, 0, ax, s);
+}
+
+template <typename T>
+ZArgs<T> z_base(const rk_handle* h) {
+  ZArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  const Chain& c = h->chain;
+  a.n_groups = c.nY;
+  int q = 0;
+  for (int g = 0; g < c.nY; ++g) {
+    a.g_begin[g] = q;
+    for (auto& t : c.zterms[g]) {
+      a.term_mz[q] = t.first;
+      a.term_p[q] = t.second;
+      ++q;
+    }
+  }
+  a.g_begin[c.nY] = q;
+  a.b = bfields<T>(h);
+  a.s = h->s;
+  a.coef = coef_of<T>(h, 2);
+  a.tw = tw_of<T>(h, 2);
+  a.nx = h->n[0];
+  a.ny = h->n[1];
+  a.nz = h->n[2];
+  a.nbox = h->nbox;
+  return a;
+}
+
+template <typename T>
+rk_status run_z(const rk_handle* h, int mode, const ZArgs<T>& a, cudaStream_t s) {
+  cudaError_t e = launch_z<T>(mode, h->n[2], a, s);
+  return e == cudaSuccess ? RK_OK : cuda_fail(e, "z pass");
+}
+
+// Alg. 2: f = out_mask o K (in_mask o d)
+template <typename T>
+rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uint8_t* out_mask, cudaStream_t s) {
+  RK_TRY(chain_forward_xy<T>(h, d, in_mask, s));
+  ZArgs<T> z = z_base<T>(h);
+  for (int g = 0; g < h->chain.nY; ++g) {
+    z.in[g] = h->ws<T>(h->chain.nX + g);
+    z.out[g] = h->ws<T>(h->chain.nX + h->chain.nY + g);
+  }
+  z.wfield = chiV<T>(h);
+  RK_TRY(run_z<T>(h, Z_STIFF, z, s));
+  return chain_reflect_yx<T>(h, f, out_mask, s);
+}
+
+// Alg. 3: u = chi o sum_p b^0_p o conv(chi o d, H^a_p)
+template <typename T>
+rk_status op_U(rk_handle* h, const T* d, T* u, cudaStream_t s) {
+  RK_TRY(chain_forward_xy<T>(h, d, h->chi, s));
+  ZArgs<T> z = z_base<T>(h);
+  for (int g = 0; g < h->chain.nY; ++g) z.in[g] = h->ws<T>(h->chain.nX + g);
+  z.out1 = u;
+  z.mask = h->chi;
+  return run_z<T>(h, Z_EVAL_U, z, s);
+}
+
+// Alg. 4 (wfield = chi V) and the transpose of Alg. 3 (wmask = chi):
+// w = chi o sum_p conv(weight o b^0_p o y, Hbar^a_p)
+template <typename T>
+rk_status op_UT(rk_handle* h, const T* y, T* w, const T* wfield, const uint8_t* wmask, cudaStream_t s) {
+  ZArgs<T> z = z_base<T>(h);
+  z.in1 = y;
+  z.wfield = wfield;
+  z.mask = wmask;
+  for (int g = 0; g < h->chain.nY; ++g) z.out[g] = h->ws<T>(h->chain.nX + h->chain.nY + g);
+  RK_TRY(run_z<T>(h, Z_TRANSPOSE_U, z, s));
+  return chain_reflect_yx<T>(h, w, h->chi, s);
+}
+
+// ------------------------------------------------------------- staging
+struct Staged {
+  const void* user;
+  void* dev;
+  size_t bytes;
+  bool host;
+};
+
+rk_status stage_in(rk_handle* h, int slot, const void* p, size_t bytes, cudaStream_t s, Staged* out) {
+  out->user = p;
+  out->bytes = bytes;
+  out->host = p && !is_device_ptr(p);
+  if (!p) {
+    out->dev = nullptr;
+    return RK_OK;
+  }
+  if (!out->host) {
+    if (((uintptr_t)p) & 15) return fail(RK_ERR_INVALID_ARG, "device array not 16-byte aligned");
+    out->dev = const_cast<void*>(p);
+    return RK_OK;
+  }
+  if (!h->stage[slot]) RK_TRY(h->alloc(&h->stage[slot], (size_t)h->nbox));
+  out->dev = h->stage[slot];
+  RK_CK(cudaMemcpyAsync(out->dev, p, bytes, cudaMemcpyHostToDevice, s));
+  return RK_OK;
+}
+
+rk_status stage_out_prepare(rk_handle* h, int slot, void* p, size_t bytes, Staged* out) {
+  out->user = p;
+  out->bytes = bytes;
+  out->host = p && !is_device_ptr(p);
+  if (!p) {
+    out->dev = nullptr;
+    return RK_OK;
+  }
+  if (!out->host) {
+    if (((uintptr_t)p) & 15) return fail(RK_ERR_INVALID_ARG, "device array not 16-byte aligned");
+    out->dev = p;
+    return RK_OK;
+  }
+  if (!h->stage[slot]) RK_TRY(h->alloc(&h->stage[slot], (size_t)h->nbox));
+  out->dev = h->stage[slot];
+  return RK_OK;
+}
+
+rk_status stage_out_finish(const Staged& st, cudaStream_t s) {
+  if (st.host && st.user) RK_CK(cudaMemcpyAsync(const_cast<void*>(st.user), st.dev, st.bytes, cudaMemcpyDeviceToHost, s));
+  return RK_OK;
+}
+
+bool any_host(std::initializer_list<const Staged*> l) {
+  for (auto* p : l)
+    if (p->host) return true;
+  return false;
+}
+
+// ------------------------------------------------------------ tables
+// Spectral multipliers of one axis: for m in [0, mmax], the DFT (Eq. 30) of the
+// wrapped table T_m(o) = (o/a~)^m phi(|o|/a~), o = -r..r (Eq. 68, 77), divided by n
+// (the 1/n of Eq. 31).  Even m: real spectrum; odd m: imaginary (stored as its
+// imaginary part).
+void axis_tables(int n, double a_tilde, int reach, int mmax, std::vector<double>& coef,
+                 std::vector<cpx<double>>& tw) {
+  coef.assign((size_t)(mmax + 1) * n, 0.0);
+  std::vector<double> T((size_t)(mmax + 1) * (reach + 1));
+  for (int m = 0; m <= mmax; ++m)
+    for (int o = 0; o <= reach; ++o) {
+      const double xi = (double)o / a_tilde;
+      T[(size_t)m * (reach + 1) + o] = std::pow(xi, m) * kernel_profile(xi);
+    }
+  for (int m = 0; m <= mmax; ++m)
+    for (int k = 0; k < n; ++k) {
+      double acc = 0.0;
+      if (m % 2 == 0) {
+        acc = T[(size_t)m * (reach + 1) + 0];
+        for (int o = 1; o <= reach; ++o) acc += 2.0 * T[(size_t)m * (reach + 1) + o] * trig::cos2pi((long long)o * k, n);
+      } else {
+        for (int o = 1; o <= reach; ++o) acc -= 2.0 * T[(size_t)m * (reach + 1) + o] * trig::sin2pi((long long)o * k, n);
+      }
+      coef[(size_t)m * n + k] = acc / (double)n;
+    }
+  tw.resize(n);
+  for (int m = 0; m < n; ++m) tw[m] = cmk(trig::cos2pi(m, n), -trig::sin2pi(m, n));
+}
+
+// Eq. 66 in discrete form: along each axis the projection of chi must leave a
+// circular run of at least `reach` empty node indices, so no two nodes of Omega
+// are within the support through the periodic boundary.
+bool gap_ok(const std::vector<uint8_t>& chi, const int n[3], int reach) {
+  for (int ax = 0; ax < 3; ++ax) {
+    std::vector<uint8_t> occ(n[ax], 0);
+    for (int k = 0; k < n[2]; ++k)
+      for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i)
+          if (chi[(size_t)i + (size_t)n[0] * ((size_t)j + (size_t)n[1] * k)]) occ[ax == 0 ? i : (ax == 1 ? j : k)] = 1;
+    int best = 0, run = 0;
+    bool any = false;
+    for (int t = 0; t < 2 * n[ax]; ++t) {
+      if (occ[t % n[ax]]) {
+        any = true;
+        run = 0;
+      } else {
+        run = std::min(run + 1, n[ax]);
+        best = std::max(best, run);
+      }
+    }
+    if (any && best < reach) return false;
+  }
+  return true;
+}
+
+template <typename T>
+void to_device_async(T* dst, const std::vector<T>& src, cudaStream_t s) {
+  cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+// ------------------------------------------------------------------ solver
+rk_status ensure_solver(rk_handle* h) {
+  if (!h->sv64) RK_TRY(h->alloc(&h->sv64, (size_t)8 * h->nbox));
+  if (!h->sv32) RK_TRY(h->alloc(&h->sv32, (size_t)4 * h->nbox));
+  if (!h->partials) RK_TRY(h->alloc(&h->partials, (size_t)kRedBlocks));
+  if (!h->dscal) RK_TRY(h->alloc(&h->dscal, (size_t)8));
+  if (!h->cg) RK_TRY(h->alloc(&h->cg, (size_t)1));
+  if (!h->hscal) {
+    void* p = nullptr;
+    RK_CK(cudaMallocHost(&p, 8 * sizeof(double)));
+    h->hscal = (double*)p;
+  }
+  return RK_OK;
+}
+
+rk_status read_scalar(rk_handle* h, const double* dptr, double* out, cudaStream_t s) {
+  RK_CK(cudaMemcpyAsync(h->hscal, dptr, sizeof(double), cudaMemcpyDeviceToHost, s));
+  RK_CK(cudaStreamSynchronize(s));
+  *out = h->hscal[0];
+  return RK_OK;
+}
+
+rk_status norm2(rk_handle* h, const double* v, double* out, cudaStream_t s) {
+  RK_CK(launch_dot<double, double>(v, v, h->nbox, h->partials, h->dscal, s));
+  double r2;
+  RK_TRY(read_scalar(h, h->dscal, &r2, s));
+  *out = std::sqrt(std::max(r2, 0.0));
+  return RK_OK;
+}
+
+// CG on the masked operator A v = chi_Omega o K(chi_Omega o v) in precision T.
+// On entry x holds the initial iterate and r = b - A x.  Stops when r.r <= rr_target.
+template <typename T>
+rk_status cg_run(rk_handle* h, T* x, T* r, T* p, T* Ap, double rr_target, int max_iter, int check_every,
+                 cudaStream_t s, int* iters, double* rr_final, int* matvecs) {
+  const long long n = h->nbox;
+  RK_CK(launch_copy<T>(p, r, n, s));
+  RK_CK(launch_dot<T, T>(r, r, n, h->partials, h->dscal, s));
+  RK_CK(launch_cg_init(h->partials, h->cg, s));
+  int it = 0;
+  double rr = 0.0;
+  for (;;) {
+    if (it % check_every == 0 || it >= max_iter) {
+      RK_CK(cudaMemcpyAsync(h->hscal, h->cg, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+      RK_CK(cudaStreamSynchronize(s));
+      CGState st;
+      memcpy(&st, h->hscal, sizeof(CGState));
+      rr = st.rr;
+      if (st.flag) {
+        *iters = it;
+        *rr_final = rr;
+        return fail(RK_ERR_BREAKDOWN, "CG breakdown (p^T A p <= 0 or not finite)");
+      }
+      if (!(rr > rr_target) || it >= max_iter) break;
+    }
+    RK_TRY(op_K<T>(h, p, Ap, h->chi_omega, h->chi_omega, s));
+    ++*matvecs;
+    RK_CK(launch_dot<T, T>(p, Ap, n, h->partials, h->dscal, s));
+    RK_CK(launch_cg_alpha(h->partials, h->cg, s));
+    RK_CK(launch_cg_xr<T>(x, r, p, Ap, h->cg, n, h->partials, s));
+    RK_CK(launch_cg_beta(h->partials, h->cg, s));
+    RK_CK(launch_cg_p<T>(p, r, h->cg, n, s));
+    ++it;
+  }
+  *iters = it;
+  *rr_final = rr;
+  return RK_OK;
+}
+
+// Solve A x = F (F already masked to chi_Omega) to ||F - A x|| <= tol ||F|| with the
+// precision of opts; x holds the initial guess (masked) on entry.
+rk_status solve_masked(rk_handle* h, const double* F, double* x, const rk_solve_opts& o, rk_solve_info* info,
+                       cudaStream_t s) {
+  const long long n = h->nbox;
+  double* r64 = h->v64(1);
+  double* p64 = h->v64(2);
+  double* Ap64 = h->v64(3);
+  double fn;
+  RK_TRY(norm2(h, F, &fn, s));
+  info->f_norm = fn;
+  if (fn == 0.0) {
+    RK_CK(launch_fill<double>(x, 0.0, n, s));
+    info->rel_residual = 0.0;
+    return RK_OK;
+  }
+  const double target = o.tol * fn;
+  auto true_residual = [&](double* rn) -> rk_status {
+    RK_TRY(op_K<double>(h, x, Ap64, h->chi_omega, h->chi_omega, s));
+    info->matvec_f64++;
+    RK_CK(launch_sub(r64, F, Ap64, n, s));
+    return norm2(h, r64, rn, s);
+  };
+  double rn;
+  RK_TRY(true_residual(&rn));
+  int total = 0;
+  if (o.precision == RK_PREC_FP64) {
+    for (int restart = 0; restart < 8 && rn > target && total < o.max_iter; ++restart) {
+      int it = 0, mv = 0;
+      double rr;
+      rk_status st = cg_run<double>(h, x, r64, p64, Ap64, target * target, o.max_iter - total, o.check_every, s, &it,
+                                   &rr, &mv);
+      total += it;
+      info->matvec_f64 += mv;
+      if (st != RK_OK) {
+        info->iterations = total;
+        return st;
+      }
+      RK_TRY(true_residual(&rn));
+    }
+  } else {
+    float* x32 = h->v32(0);
+    float* r32 = h->v32(1);
+    float* p32 = h->v32(2);
+    float* Ap32 = h->v32(3);
+    double prev = rn;
+    int stall = 0;
+    while (rn > target && info->outer < o.max_outer && total < o.max_iter) {
+      // inner FP32 solve of A c = r / |r|, to relative residual inner_tol
+      RK_CK(launch_to_f32(r32, r64, 1.0 / rn, n, s));
+      RK_CK(launch_fill<float>(x32, 0.0f, n, s));
+      const double it_tol = std::max(o.inner_tol, 0.5 * target / rn);
+      int it = 0, mv = 0;
+      double rr;
+      rk_status st = cg_run<float>(h, x32, r32, p32, Ap32, it_tol * it_tol, o.max_iter - total, o.check_every, s,
+                                  &it, &rr, &mv);
+      total += it;
+      info->matvec_f32 += mv;
+      info->outer++;
+      if (st != RK_OK && st != RK_ERR_BREAKDOWN) return st;
+      RK_CK(launch_acc_f32(x, x32, rn, n, s));
+      RK_TRY(true_residual(&rn));
+      if (rn > 0.9 * prev) {
+        if (++stall >= 3) break;
+      } else {
+        stall = 0;
+      }
+      prev = rn;
+    }
+  }
+  info->iterations = total;
+  info->rel_residual = rn / fn;
+  if (rn > target) return fail(RK_ERR_NOT_CONVERGED, "tolerance not reached");
+  return RK_OK;
+}
+
+void fill_defaults(rk_solve_opts* o) {
+  o->tol = 1e-10;
+  o->max_iter = 200000;
+  o->precision = RK_PREC_MIXED;
+  o->inner_tol = 1e-4;
+  o->max_outer = 60;
+  o->check_every = 25;
+  o->x0_given = 0;
+  o->reserved = 0;
+}
+
+rk_status check_opts(const rk_solve_opts& o) {
+  if (!(o.tol > 0.0) || o.max_iter < 1 || (o.precision != RK_PREC_FP64 && o.precision != RK_PREC_MIXED) ||
+      !(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.max_outer < 1 || o.check_every < 1)
+    return fail(RK_ERR_INVALID_ARG, "invalid solve options");
+  return RK_OK;
+}
+
+// The forward solve of Alg. 5: d = d_Gamma + x, x on chi_Omega.  Vectors in the
+// handle: F = v64(4), d0 = v64(5).
+rk_status forward_solve(rk_handle* h, const double* r, const double* g, double* d, const rk_solve_opts& o,
+                        rk_solve_info* info, cudaStream_t s) {
+  const long long n = h->nbox;
+  double* F = h->v64(4);
+  double* d0 = h->v64(5);
+  double* t0 = h->v64(6);
+  double* x = h->v64(0);
+  // d_Gamma = g on chi_gamma (Eq. 29)
+  if (g)
+    RK_CK(launch_dirichlet_d0(d0, g, h->chi_gamma, n, s));
+  else
+    RK_CK(launch_fill<double>(d0, 0.0, n, s));
+  // f^r (Alg. 4) and F = chi_Omega o (f^r - K d_Gamma)
+  RK_TRY(op_UT<double>(h, r, t0, h->chiV64, nullptr, s));
+  RK_TRY(op_K<double>(h, d0, F, h->chi, h->chi_omega, s));
+  info->matvec_f64++;
+  RK_CK(launch_masked_diff(F, t0, F, h->chi_omega, n, s));
+  if (o.x0_given)
+    RK_CK(launch_mask(x, d, h->chi_omega, n, s));
+  else
+    RK_CK(launch_fill<double>(x, 0.0, n, s));
+  rk_status st = solve_masked(h, F, x, o, info, s);
+  RK_CK(launch_add(d, d0, x, n, s));
+  return st;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+void rk_default_solve_opts(rk_solve_opts* opts) {
+  if (opts) fill_defaults(opts);
+}
+
+int rk_supported_length(int n) { return supported_length(n) ? 1 : 0; }
+
+const char* rk_status_string(rk_status s) {
+  switch (s) {
+    case RK_OK: return "RK_OK";
+    case RK_ERR_INVALID_ARG: return "RK_ERR_INVALID_ARG";
+    case RK_ERR_CUDA: return "RK_ERR_CUDA";
+    case RK_ERR_OOM: return "RK_ERR_OOM";
+    case RK_ERR_SINGULAR_MOMENT: return "RK_ERR_SINGULAR_MOMENT";
+    case RK_ERR_NOT_CONVERGED: return "RK_ERR_NOT_CONVERGED";
+    case RK_ERR_BREAKDOWN: return "RK_ERR_BREAKDOWN";
+    case RK_ERR_TIMEOUT: return "RK_ERR_TIMEOUT";
+    case RK_ERR_UNSUPPORTED: return "RK_ERR_UNSUPPORTED";
+  }
+  return "RK_ERR_UNKNOWN";
+}
+
+const char* rk_last_error_message(void) { return g_err.c_str(); }
+
+rk_status rk_destroy(rk_handle* h) {
+  if (!h) return RK_OK;
+  for (void* p : h->owned) cudaFree(p);
+  if (h->hscal) cudaFreeHost(h->hscal);
+  delete h;
+  return RK_OK;
+}
+
+rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_gamma, const double* V,
+                   int32_t degree, double a_tilde, void* stream, rk_handle** out) {
+  g_err.clear();
+  if (!out) return fail(RK_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid || !chi || !V) return fail(RK_ERR_INVALID_ARG, "grid, chi and V are required");
+  if (degree != 1 && degree != 2) return fail(RK_ERR_INVALID_ARG, "degree must be 1 or 2");
+  if (!(a_tilde > 0.5 && a_tilde < 16.0)) return fail(RK_ERR_INVALID_ARG, "a_tilde out of range");
+  for (int k = 0; k < 3; ++k) {
+    if (grid->n[k] < 2 || !(grid->h[k] > 0.0)) return fail(RK_ERR_INVALID_ARG, "bad grid");
+    if (!supported_length(grid->n[k]))
+      return fail(RK_ERR_UNSUPPORTED, "box side " + std::to_string(grid->n[k]) + " not built");
+  }
+  if (grid->n[0] % 2 != 0 || ((long long)grid->n[1] * grid->n[2]) % 2 != 0)
+    return fail(RK_ERR_UNSUPPORTED, "n[0] and n[1]*n[2] must be even");
+  cudaStream_t s = (cudaStream_t)stream;
+  rk_handle* h = new rk_handle();
+  auto bail = [&](rk_status st) {
+    rk_destroy(h);
+    return st;
+  };
+  for (int k = 0; k < 3; ++k) {
+    h->n[k] = grid->n[k];
+    h->h[k] = grid->h[k];
+  }
+  h->a_tilde = a_tilde;
+  h->degree = degree;
+  h->s = degree == 1 ? 4 : 10;
+  h->nbox = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+  cudaGetDevice(&h->device);
+  h->chain.build(degree);
+  int reach = 0;
+  while (kernel_profile((double)(reach + 1) / a_tilde) > 0.0) ++reach;
+  h->reach = reach;
+  for (int k = 0; k < 3; ++k)
+    if (2 * reach + 1 > h->n[k]) return bail(fail(RK_ERR_UNSUPPORTED, "support wider than the box"));
+  const long long n = h->nbox;
+
+  // inputs to the device; host copy of chi for the gap check
+  rk_status st;
+  if ((st = h->alloc(&h->chi, n)) || (st = h->alloc(&h->chi_gamma, n)) || (st = h->alloc(&h->chi_omega, n)) ||
+      (st = h->alloc(&h->V, n)) || (st = h->alloc(&h->chiV64, n)) || (st = h->alloc(&h->chiV32, n)) ||
+      (st = h->alloc(&h->b64, (size_t)4 * h->s * n)) || (st = h->alloc(&h->b32, (size_t)4 * h->s * n)) ||
+      (st = h->alloc(&h->ws64, (size_t)ws_fields(h->chain) * n)) ||
+      (st = h->alloc(&h->ws32, (size_t)ws_fields(h->chain) * n)) || (st = h->alloc(&h->counters, 2)))
+    return bail(st);
+  std::vector<uint8_t> hchi(n), hgam(n, 0), homg(n);
+  cudaError_t e = cudaMemcpy(hchi.data(), chi, n, cudaMemcpyDefault);
+  if (e == cudaSuccess && chi_gamma) e = cudaMemcpy(hgam.data(), chi_gamma, n, cudaMemcpyDefault);
+  if (e == cudaSuccess) e = cudaMemcpy(h->V, V, n * sizeof(double), cudaMemcpyDefault);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "copy inputs"));
+  long long nom = 0;
+  for (long long i = 0; i < n; ++i) {
+    hchi[i] = hchi[i] ? 1 : 0;
+    hgam[i] = (hgam[i] && hchi[i]) ? 1 : 0;
+    homg[i] = hchi[i] & (uint8_t)(1 - hgam[i]);
+    nom += hchi[i];
+  }
+  h->n_omega = nom;
+  if (!gap_ok(hchi, h->n, reach))
+    return bail(fail(RK_ERR_UNSUPPORTED, "gap between the domain and its periodic image is narrower than the support (Eq. 66)"));
+  e = cudaMemcpy(h->chi, hchi.data(), n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->chi_gamma, hgam.data(), n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->chi_omega, homg.data(), n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "copy masks"));
+
+  // per-axis tables for m in [0, 2 deg] (moments need 2 deg; the chains use <= deg)
+  const int mmax = 2 * degree;
+  for (int k = 0; k < 3; ++k) {
+    std::vector<double> coef;
+    std::vector<cpx<double>> tw;
+    axis_tables(h->n[k], a_tilde, reach, mmax, coef, tw);
+    std::vector<float> coef32(coef.begin(), coef.end());
+    std::vector<cpx<float>> tw32(tw.size());
+    for (size_t i = 0; i < tw.size(); ++i) tw32[i] = cmk((float)tw[i].x, (float)tw[i].y);
+    if ((st = h->alloc(&h->coef64[k], coef.size())) || (st = h->alloc(&h->coef32[k], coef.size())) ||
+        (st = h->alloc(&h->tw64[k], tw.size())) || (st = h->alloc(&h->tw32[k], tw.size())))
+      return bail(st);
+    e = cudaMemcpy(h->coef64[k], coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->coef32[k], coef32.data(), coef32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->tw64[k], tw.data(), tw.size() * sizeof(cpx<double>), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->tw32[k], tw32.data(), tw32.size() * sizeof(cpx<float>), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "copy tables"));
+  }
+
+  // ---- Alg. 1: moment fields m_gamma = chi (*) prod_k T_{gamma_k}, |gamma| <= 2 deg
+  const int D2 = 2 * degree;
+  std::vector<std::pair<int, int>> ylist;      // (gx, gy)
+  std::vector<std::array<int, 3>> zlist;       // (gx, gy, gz)
+  for (int gx = 0; gx <= D2; ++gx)
+    for (int gy = 0; gx + gy <= D2; ++gy) ylist.push_back({gx, gy});
+  std::vector<int> zbegin;
+  for (auto& yg : ylist) {
+    zbegin.push_back((int)zlist.size());
+    for (int gz = 0; yg.first + yg.second + gz <= D2; ++gz) zlist.push_back({yg.first, yg.second, gz});
+  }
+  const int nXm = D2 + 1, nYm = (int)ylist.size(), nZm = (int)zlist.size();
+  double* mws = nullptr;
+  e = cudaMalloc((void**)&mws, sizeof(double) * (size_t)(1 + nXm + nYm + nZm) * n);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "set-up workspace"));
+  auto mf = [&](int i) { return mws + (size_t)i * n; };
+  auto run_setup = [&]() -> rk_status {
+    RK_CK(launch_u8_to_f64(mf(0), h->chi, n, s));
+    PassArgs<double> ax = pass_base<double>(h, 0);
+    ax.in[0] = mf(0);
+    ax.n_groups = 1;
+    ax.g_io[0] = 0;
+    ax.g_begin[0] = 0;
+    for (int m = 0; m < nXm; ++m) {
+      ax.out[m] = mf(1 + m);
+      ax.term_io[m] = m;
+      ax.term_m[m] = m;
+    }
+    ax.g_begin[1] = nXm;
+    RK_TRY(run_split<double>(h, 0, ax, s));
+    PassArgs<double> ay = pass_base<double>(h, 1);
+    ay.n_groups = nXm;
+    int q = 0;
+    for (int gx = 0; gx < nXm; ++gx) {
+      ay.in[gx] = mf(1 + gx);
+      ay.g_io[gx] = gx;
+      ay.g_begin[gx] = q;
+      for (int yi = 0; yi < nYm; ++yi)
+        if (ylist[yi].first == gx) {
+          ay.out[yi] = mf(1 + nXm + yi);
+          ay.term_io[q] = yi;
+          ay.term_m[q] = ylist[yi].second;
+          ++q;
+        }
+    }
+    ay.g_begin[nXm] = q;
+    RK_TRY(run_split<double>(h, 1, ay, s));
+    PassArgs<double> az = pass_base<double>(h, 2);
+    az.n_groups = nYm;
+    q = 0;
+    for (int yi = 0; yi < nYm; ++yi) {
+      az.in[yi] = mf(1 + nXm + yi);
+      az.g_io[yi] = yi;
+      az.g_begin[yi] = q;
+      for (int zi = zbegin[yi]; zi < (yi + 1 < nYm ? zbegin[yi + 1] : nZm); ++zi) {
+        az.out[zi] = mf(1 + nXm + nYm + zi);
+        az.term_io[q] = zi;
+        az.term_m[q] = zlist[zi][2];
+        ++q;
+      }
+    }
+    az.g_begin[nYm] = q;
+    RK_TRY(run_split<double>(h, 2, az, s));
+    // per-node M^{-1} -> b (Eq. 83-85)
+    MomentArgs ma;
+    memset(&ma, 0, sizeof(ma));
+    ma.mom = mf(1 + nXm + nYm);
+    ma.n_mom = nZm;
+    ma.s = h->s;
+    const Chain& c = h->chain;
+    for (int p = 0; p < h->s; ++p)
+      for (int qq = 0; qq < h->s; ++qq) {
+        int gam[3] = {c.alpha[p][0] + c.alpha[qq][0], c.alpha[p][1] + c.alpha[qq][1], c.alpha[p][2] + c.alpha[qq][2]};
+        int idx = -1;
+        for (int zi = 0; zi < nZm; ++zi)
+          if (zlist[zi][0] == gam[0] && zlist[zi][1] == gam[1] && zlist[zi][2] == gam[2]) idx = zi;
+        ma.pq[p][qq] = (signed char)idx;
+      }
+    ma.chi = h->chi;
+    for (int k = 0; k < 3; ++k) ma.inv_a[k] = 1.0 / (a_tilde * h->h[k]);
+    ma.V = h->V;
+    ma.b64 = h->b64;
+    ma.b32 = h->b32;
+    ma.chiV64 = h->chiV64;
+    ma.chiV32 = h->chiV32;
+    ma.nbox = n;
+    ma.n_singular = h->counters;
+    ma.first_singular = h->counters + 1;
+    unsigned long long init[2] = {0ull, ~0ull};
+    RK_CK(cudaMemcpyAsync(h->counters, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    RK_CK(launch_moment_solve(ma, s));
+    unsigned long long res[2];
+    RK_CK(cudaMemcpyAsync(res, h->counters, sizeof(res), cudaMemcpyDeviceToHost, s));
+    RK_CK(cudaStreamSynchronize(s));
+    h->n_singular = (long long)res[0];
+    h->first_singular = res[0] ? (long long)res[1] : -1;
+    return RK_OK;
+  };
+  st = run_setup();
+  cudaFree(mws);
+  if (st != RK_OK) return bail(st);
+  *out = h;
+  if (h->n_singular)
+    return fail(RK_ERR_SINGULAR_MOMENT,
+                std::to_string(h->n_singular) + " singular moment matrices, first at " + std::to_string(h->first_singular));
+  return RK_OK;
+}
+
+rk_status rk_singular_nodes(const rk_handle* h, int64_t* count, int64_t* first) {
+  if (!h) return fail(RK_ERR_INVALID_ARG, "handle is NULL");
+  if (count) *count = h->n_singular;
+  if (first) *first = h->first_singular;
+  return RK_OK;
+}
+
+rk_status rk_get_shape(const rk_handle* h, int32_t n[3], int32_t* s, int64_t* n_omega) {
+  if (!h) return fail(RK_ERR_INVALID_ARG, "handle is NULL");
+  if (n)
+    for (int k = 0; k < 3; ++k) n[k] = h->n[k];
+  if (s) *s = h->s;
+  if (n_omega) *n_omega = h->n_omega;
+  return RK_OK;
+}
+
+rk_status rk_apply_K(rk_handle* h, const void* d, void* f, int32_t dtype, void* stream) {
+  if (!h || !d || !f) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  if (dtype != RK_F64 && dtype != RK_F32) return fail(RK_ERR_INVALID_ARG, "bad dtype");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * (dtype == RK_F64 ? 8 : 4);
+  Staged sd, sf;
+  RK_TRY(stage_in(h, 0, d, bytes, s, &sd));
+  RK_TRY(stage_out_prepare(h, 1, f, bytes, &sf));
+  if (dtype == RK_F64)
+    RK_TRY(op_K<double>(h, (const double*)sd.dev, (double*)sf.dev, h->chi, h->chi, s));
+  else
+    RK_TRY(op_K<float>(h, (const float*)sd.dev, (float*)sf.dev, h->chi, h->chi, s));
+  RK_TRY(stage_out_finish(sf, s));
+  if (any_host({&sd, &sf})) RK_CK(cudaStreamSynchronize(s));
+  return RK_OK;
+}
+
+rk_status rk_rhs(rk_handle* h, const double* r, double* fr, void* stream) {
+  if (!h || !r || !fr) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * 8;
+  Staged a, b;
+  RK_TRY(stage_in(h, 0, r, bytes, s, &a));
+  RK_TRY(stage_out_prepare(h, 1, fr, bytes, &b));
+  RK_TRY(op_UT<double>(h, (const double*)a.dev, (double*)b.dev, h->chiV64, nullptr, s));
+  RK_TRY(stage_out_finish(b, s));
+  if (any_host({&a, &b})) RK_CK(cudaStreamSynchronize(s));
+  return RK_OK;
+}
+
+rk_status rk_eval_u(rk_handle* h, const double* d, double* u, void* stream) {
+  if (!h || !d || !u) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * 8;
+  Staged a, b;
+  RK_TRY(stage_in(h, 0, d, bytes, s, &a));
+  RK_TRY(stage_out_prepare(h, 1, u, bytes, &b));
+  RK_TRY(op_U<double>(h, (const double*)a.dev, (double*)b.dev, s));
+  RK_TRY(stage_out_finish(b, s));
+  if (any_host({&a, &b})) RK_CK(cudaStreamSynchronize(s));
+  return RK_OK;
+}
+
+rk_status rk_eval_u_transpose(rk_handle* h, const double* ev, double* w, void* stream) {
+  if (!h || !ev || !w) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * 8;
+  Staged a, b;
+  RK_TRY(stage_in(h, 0, ev, bytes, s, &a));
+  RK_TRY(stage_out_prepare(h, 1, w, bytes, &b));
+  RK_TRY(op_UT<double>(h, (const double*)a.dev, (double*)b.dev, nullptr, h->chi, s));
+  RK_TRY(stage_out_finish(b, s));
+  if (any_host({&a, &b})) RK_CK(cudaStreamSynchronize(s));
+  return RK_OK;
+}
+
+rk_status rk_get_b(rk_handle* h, double* b, void* stream) {
+  if (!h || !b) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  RK_CK(cudaMemcpyAsync(b, h->b64, sizeof(double) * (size_t)4 * h->s * h->nbox, cudaMemcpyDefault, s));
+  if (!is_device_ptr(b)) RK_CK(cudaStreamSynchronize(s));
+  return RK_OK;
+}
+
+rk_status rk_solve(rk_handle* h, const double* r, const double* g, double* d, double* u, const rk_solve_opts* opts,
+                   rk_solve_info* info, void* stream) {
+  if (!h || !r || !d) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  rk_solve_opts o;
+  if (opts)
+    o = *opts;
+  else
+    fill_defaults(&o);
+  RK_TRY(check_opts(o));
+  rk_solve_info inf;
+  memset(&inf, 0, sizeof(inf));
+  cudaStream_t s = (cudaStream_t)stream;
+  RK_TRY(ensure_solver(h));
+  auto t0 = std::chrono::steady_clock::now();
+  const size_t bytes = (size_t)h->nbox * 8;
+  Staged sr, sg, sd, su;
+  RK_TRY(stage_in(h, 0, r, bytes, s, &sr));
+  RK_TRY(stage_in(h, 1, g, bytes, s, &sg));
+  if (o.x0_given)
+    RK_TRY(stage_in(h, 2, d, bytes, s, &sd));
+  else
+    RK_TRY(stage_out_prepare(h, 2, d, bytes, &sd));
+  RK_TRY(stage_out_prepare(h, 3, u, bytes, &su));
+  rk_status st = forward_solve(h, (const double*)sr.dev, (const double*)sg.dev, (double*)sd.dev, o, &inf, s);
+  if (st == RK_OK || st == RK_ERR_NOT_CONVERGED || st == RK_ERR_BREAKDOWN) {
+    if (su.dev) RK_TRY(op_U<double>(h, (const double*)sd.dev, (double*)su.dev, s));
+    RK_TRY(stage_out_finish(sd, s));
+    RK_TRY(stage_out_finish(su, s));
+  }
+  RK_CK(cudaStreamSynchronize(s));
+  inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  inf.status = st;
+  if (info) *info = inf;
+  return st;
+}
+
+rk_status rk_solve_adjoint(rk_handle* h, const double* r, const double* g, const double* u_target, double* dJ_dr,
+                           double* dJ_dg, double* J, const rk_solve_opts* opts, rk_solve_info* info, void* stream) {
+  if (!h || !r || !u_target || !dJ_dr || !dJ_dg) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  rk_solve_opts o;
+  if (opts)
+    o = *opts;
+  else
+    fill_defaults(&o);
+  o.x0_given = 0;
+  RK_TRY(check_opts(o));
+  rk_solve_info inf;
+  memset(&inf, 0, sizeof(inf));
+  cudaStream_t s = (cudaStream_t)stream;
+  RK_TRY(ensure_solver(h));
+  auto t0 = std::chrono::steady_clock::now();
+  const long long n = h->nbox;
+  const size_t bytes = (size_t)n * 8;
+  Staged sr, sg, sut, sdr, sdg;
+  RK_TRY(stage_in(h, 0, r, bytes, s, &sr));
+  RK_TRY(stage_in(h, 1, g, bytes, s, &sg));
+  RK_TRY(stage_in(h, 2, u_target, bytes, s, &sut));
+  RK_TRY(stage_out_prepare(h, 3, dJ_dr, bytes, &sdr));
+  RK_TRY(stage_out_prepare(h, 4, dJ_dg, bytes, &sdg));
+  double* dvec = h->v64(7);
+  double* uvec = (double*)sdr.dev;  // scratch until dJ/dr is written
+  double* e = (double*)sdg.dev;     // scratch until dJ/dg is written
+  // forward solve (recomputed from r, g)
+  rk_status st = forward_solve(h, (const double*)sr.dev, (const double*)sg.dev, dvec, o, &inf, s);
+  if (st != RK_OK) {
+    inf.status = st;
+    if (info) *info = inf;
+    return st;
+  }
+  RK_TRY(op_U<double>(h, dvec, uvec, s));
+  // e = chi o (u - u_target); J = 1/2 e.e
+  RK_CK(launch_sub(e, uvec, (const double*)sut.dev, n, s));
+  RK_CK(launch_mask(e, e, h->chi, n, s));
+  double ee;
+  RK_CK(launch_dot<double, double>(e, e, n, h->partials, h->dscal, s));
+  RK_TRY(read_scalar(h, h->dscal, &ee, s));
+  if (J) *J = 0.5 * ee;
+  // w = U^T e; adjoint solve A lambda = chi_Omega o w
+  double* w = h->v64(6);
+  double* F = h->v64(4);
+  double* lam = h->v64(0);
+  RK_TRY(op_UT<double>(h, e, w, nullptr, h->chi, s));
+  RK_CK(launch_mask(F, w, h->chi_omega, n, s));
+  RK_CK(launch_fill<double>(lam, 0.0, n, s));
+  rk_solve_info ainf;
+  memset(&ainf, 0, sizeof(ainf));
+  st = solve_masked(h, F, lam, o, &ainf, s);
+  inf.iterations += ainf.iterations;
+  inf.outer += ainf.outer;
+  inf.matvec_f32 += ainf.matvec_f32;
+  inf.matvec_f64 += ainf.matvec_f64;
+  inf.rel_residual = std::max(inf.rel_residual, ainf.rel_residual);
+  if (st != RK_OK) {
+    inf.status = st;
+    if (info) *info = inf;
+    return st;
+  }
+  // dJ/dg = chi_gamma o (w - K lambda)
+  double* Klam = h->v64(3);
+  RK_TRY(op_K<double>(h, lam, Klam, h->chi, h->chi_gamma, s));
+  RK_CK(launch_masked_diff(e, w, Klam, h->chi_gamma, n, s));
+  // dJ/dr = chi V o U lambda
+  RK_TRY(op_U<double>(h, lam, uvec, s));
+  RK_CK(launch_mul(uvec, h->chiV64, n, s));
+  RK_TRY(stage_out_finish(sdr, s));
+  RK_TRY(stage_out_finish(sdg, s));
+  RK_CK(cudaStreamSynchronize(s));
+  inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  inf.status = RK_OK;
+  if (info) *info = inf;
+  return RK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// rk_moment.cuh -- per-node moment solve of Alg. 1 (kernel body shared by the
+// library build).
+#pragma once
+
+#include "rk_internal.cuh"
+
+namespace rk {
+
+// ---------------------------------------------------------------- Alg. 1 tail
+// One thread per node: assemble M(x) from the moment fields (Eq. 48/80; M = I off
+// chi), Cholesky factorisation in FP64, rows 1..4 of M^{-1} by two triangular
+// solves, then b^0 = row 1, b^k = -(1/a_k) row (1+k) (Eq. 83-85, scaled basis).
+// A pivot <= 1e-14 * trace(M) marks the node singular: its b are set to 0 and the
+// node is counted.
+__global__ void __launch_bounds__(128) k_moment_solve(const MomentArgs a) {
+  const int s = a.s;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.nbox;
+       i += (long long)gridDim.x * blockDim.x) {
+    double L[kMaxS * (kMaxS + 1) / 2];  // packed lower triangle, row-major
+    const bool in = a.chi[i] != 0;
+    double tr = 0.0;
+    for (int p = 0; p < s; ++p)
+      for (int q = 0; q <= p; ++q) {
+        double v = in ? a.mom[(long long)a.pq[p][q] * a.nbox + i] : (p == q ? 1.0 : 0.0);
+        L[p * (p + 1) / 2 + q] = v;
+        if (p == q) tr += fabs(v);
+      }
+    bool bad = false;
+    for (int j = 0; j < s && !bad; ++j) {
+      double d = L[j * (j + 1) / 2 + j];
+      for (int k = 0; k < j; ++k) d -= L[j * (j + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+      if (!(d > 1e-14 * tr)) {
+        bad = true;
+        break;
+      }
+      const double l = sqrt(d);
+      L[j * (j + 1) / 2 + j] = l;
+      for (int r = j + 1; r < s; ++r) {
+        double v = L[r * (r + 1) / 2 + j];
+        for (int k = 0; k < j; ++k) v -= L[r * (r + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+        L[r * (r + 1) / 2 + j] = v / l;
+      }
+    }
+    if (bad) {
+      atomicAdd(a.n_singular, 1ull);
+      atomicMin(a.first_singular, (unsigned long long)i);
+    }
+    for (int row = 0; row < 4; ++row) {
+      double x[kMaxS];
+      for (int p = 0; p < s; ++p) x[p] = (p == row) ? 1.0 : 0.0;
+      if (!bad) {
+        for (int p = 0; p < s; ++p) {
+          double v = x[p];
+          for (int k = 0; k < p; ++k) v -= L[p * (p + 1) / 2 + k] * x[k];
+          x[p] = v / L[p * (p + 1) / 2 + p];
+        }
+        for (int p = s - 1; p >= 0; --p) {
+          double v = x[p];
+          for (int k = p + 1; k < s; ++k) v -= L[k * (k + 1) / 2 + p] * x[k];
+          x[p] = v / L[p * (p + 1) / 2 + p];
+        }
+      } else {
+        for (int p = 0; p < s; ++p) x[p] = 0.0;
+      }
+      const double sc = row == 0 ? 1.0 : -a.inv_a[row - 1];
+      for (int p = 0; p < s; ++p) {
+        const double v = sc * x[p];
+        const long long o = ((long long)row * s + p) * a.nbox + i;
+        a.b64[o] = v;
+        if (a.b32) a.b32[o] = (float)v;
+      }
+    }
+    const double cv = in ? a.V[i] : 0.0;
+    a.chiV64[i] = cv;
+    if (a.chiV32) a.chiV32[i] = (float)cv;
+  }
+}
+
+}  // namespace rk

@@ -1,0 +1,399 @@
+// rk_passes.cuh -- axis passes of the FC-RKPM convolutions.
+//
+// Every convolving array of the method is a tensor product of 1D tables:
+// H^a_p(x) = prod_k T^{(k)}_{alpha_k(p)}(x_k) with T_m(o) = (o/a~)^m phi(|o|/a~)
+// (Eq. 6, 44, 77), and H_p H^a_q = prod_k T_{alpha_k(p)+alpha_k(q)} (Eq. 80).
+// Its DFT (Eq. 30) is the product of the 1D DFTs, so each 3D fast convolution
+// F^{-1}[F(a) o F(H)] of Eq. 34 factors into three 1D circular convolutions, one
+// per axis, each done as forward FFT -> multiply -> inverse FFT along that axis.
+// A pass applies one axis for several (input, table) pairs at once:
+//   SPLIT: each input line is transformed once and convolved with several tables
+//          (one output per table)                -- the forward chain of Alg. 1-3;
+//   MERGE: several inputs, each with its table, are summed in the spectrum and
+//          transformed back once                 -- the reflected chain of Alg. 2, 4.
+// The z pass of Alg. 2 additionally performs the pointwise stage between the two
+// chains (A^k = sum_q b^k_q D_q, Eq. 90; C^k_p A^k, Eq. 91) without leaving the
+// chip.
+//
+// Data: real fields on the periodic box, x fastest (idx = i + nx*(j + ny*k)).
+// Two real lines are packed into one complex line (re = line 0, im = line 1);
+// the tables are real even/odd sequences, so convolution keeps the two apart.
+//   x lines: pairs of consecutive rows (row r = j + ny*k), P threads per line;
+//   y and z lines: pairs of adjacent x (a float2/double2 per node pair).
+#pragma once
+
+#include "rk_linefft.cuh"
+
+namespace rk {
+
+constexpr int kMaxIn = 16;   // input fields of one pass
+constexpr int kMaxOut = 40;  // output fields (or terms) of one pass
+
+// Spectral multiplier of table m at spectral index k:  coef[m*N + k] is real for
+// even m (even table) and the imaginary part for odd m (odd table).  The 1/N of
+// the inverse transform is included.  reflect selects H-bar (Eq. 55): (-1)^m.
+template <typename T>
+RK_HD cpx<T> spec_mul(cpx<T> v, const T* __restrict__ coef, int N, int m, int k, int reflect) {
+  T c = coef[m * N + k];
+  if (reflect && (m & 1)) c = -c;
+  return (m & 1) ? ciscale(v, c) : cscale(v, c);
+}
+
+template <typename T>
+struct PassArgs {
+  const T* in[kMaxIn];
+  T* out[kMaxOut];
+  int n_groups;
+  int g_io[kMaxOut];          // SPLIT: input index of group g; MERGE: output index
+  int g_begin[kMaxOut + 1];   // terms of group g
+  int term_io[kMaxOut];       // SPLIT: output index of the term; MERGE: input index
+  int term_m[kMaxOut];        // table (monomial power) of the term
+  const T* coef;              // spectral multipliers of this axis, [mmax+1][N]
+  const cpx<T>* tw;           // twiddles of this axis, [N]
+  int reflect;
+  const uint8_t* in_mask;     // optional: inputs multiplied by mask (x pass only)
+  const uint8_t* out_mask;    // optional: outputs multiplied by mask (x pass only)
+  int nx, ny, nz;
+  long long line_stride;      // strided passes: element stride along the line
+  long long other_stride;     // strided passes: stride of blockIdx.y
+};
+
+// ---------------------------------------------------------------- strided passes
+// Block: L node pairs (2L adjacent x) times P threads per line; thread (t, l) with
+// l = threadIdx.x % L fastest, so a warp reads 2L contiguous values per line
+// position.
+template <typename T, int N, int L>
+struct Strided {
+  using F = LineFFT<T, N>;
+  using V2 = typename vec2<T>::type;
+  static constexpr int P = F::P, R = F::R;
+  static constexpr int THREADS = L * P;
+  static constexpr size_t SMEM = sizeof(cpx<T>) * (size_t)N * L;
+
+  RK_DEV static cpx<T> load(const T* p, long long off) {
+    V2 v = RK_LDG(reinterpret_cast<const V2*>(p + off));
+    return cmk(v.x, v.y);
+  }
+  RK_DEV static void store(T* p, long long off, cpx<T> v) {
+    V2 w;
+    w.x = v.x;
+    w.y = v.y;
+    *reinterpret_cast<V2*>(p + off) = w;
+  }
+};
+
+template <typename T, int N, int L>
+__global__ void __launch_bounds__(Strided<T, N, L>::THREADS)
+    k_strided_split(const PassArgs<T> a) {
+  using S = Strided<T, N, L>;
+  using F = typename S::F;
+  RK_DYN_SMEM(cpx<T>, sm);
+  const int l = threadIdx.x % L, t = threadIdx.x / L;
+  const int x = blockIdx.x * 2 * L + 2 * l;
+  const bool ok = x < a.nx;
+  const long long base = (long long)x + (long long)blockIdx.y * a.other_stride;
+  InterleavedBuf<T, F::N1, F::N2> buf{sm + l, L};
+  cpx<T> v[S::R], w[S::R];
+  for (int g = 0; g < a.n_groups; ++g) {
+    const T* in = a.in[a.g_io[g]];
+#pragma unroll
+    for (int r = 0; r < S::R; ++r)
+      v[r] = ok ? S::load(in, base + F::nat_pos(t, r) * a.line_stride) : cmk((T)0, (T)0);
+    F::forward(v, t, buf, a.tw);
+    for (int q = a.g_begin[g]; q < a.g_begin[g + 1]; ++q) {
+      const int m = a.term_m[q];
+#pragma unroll
+      for (int r = 0; r < S::R; ++r) w[r] = spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
+      F::inverse(w, t, buf, a.tw);
+      T* out = a.out[a.term_io[q]];
+      if (ok)
+#pragma unroll
+        for (int r = 0; r < S::R; ++r) S::store(out, base + F::nat_pos(t, r) * a.line_stride, w[r]);
+    }
+  }
+}
+
+template <typename T, int N, int L>
+__global__ void __launch_bounds__(Strided<T, N, L>::THREADS)
+    k_strided_merge(const PassArgs<T> a) {
+  using S = Strided<T, N, L>;
+  using F = typename S::F;
+  RK_DYN_SMEM(cpx<T>, sm);
+  const int l = threadIdx.x % L, t = threadIdx.x / L;
+  const int x = blockIdx.x * 2 * L + 2 * l;
+  const bool ok = x < a.nx;
+  const long long base = (long long)x + (long long)blockIdx.y * a.other_stride;
+  InterleavedBuf<T, F::N1, F::N2> buf{sm + l, L};
+  cpx<T> v[S::R], acc[S::R];
+  for (int g = 0; g < a.n_groups; ++g) {
+#pragma unroll
+    for (int r = 0; r < S::R; ++r) acc[r] = cmk((T)0, (T)0);
+    for (int q = a.g_begin[g]; q < a.g_begin[g + 1]; ++q) {
+      const T* in = a.in[a.term_io[q]];
+      const int m = a.term_m[q];
+#pragma unroll
+      for (int r = 0; r < S::R; ++r)
+        v[r] = ok ? S::load(in, base + F::nat_pos(t, r) * a.line_stride) : cmk((T)0, (T)0);
+      F::forward(v, t, buf, a.tw);
+#pragma unroll
+      for (int r = 0; r < S::R; ++r) acc[r] = acc[r] + spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
+    }
+    F::inverse(acc, t, buf, a.tw);
+    T* out = a.out[a.g_io[g]];
+    if (ok)
+#pragma unroll
+      for (int r = 0; r < S::R; ++r) S::store(out, base + F::nat_pos(t, r) * a.line_stride, acc[r]);
+  }
+}
+
+// ------------------------------------------------------------------- x passes
+// Block: LX pairs of rows times P threads per line; thread (t, l) with t fastest so
+// that the P threads of a line read P consecutive x.
+template <typename T, int N, int LX>
+struct XPass {
+  using F = LineFFT<T, N>;
+  using B = PaddedBuf<T, F::N1, F::N2>;
+  static constexpr int P = F::P, R = F::R;
+  static constexpr int THREADS = LX * P;
+  static constexpr size_t SMEM = sizeof(cpx<T>) * (size_t)B::SIZE * LX;
+};
+
+template <typename T>
+RK_DEV T mask_of(const uint8_t* m, long long i) {
+  return m ? (T)RK_LDG(m + i) : (T)1;
+}
+
+template <typename T, int N, int LX>
+__global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_split(const PassArgs<T> a) {
+  using X = XPass<T, N, LX>;
+  using F = typename X::F;
+  RK_DYN_SMEM(cpx<T>, sm);
+  const int t = threadIdx.x % X::P, l = threadIdx.x / X::P;
+  const long long q = (long long)blockIdx.x * LX + l;  // row pair
+  const long long npairs = ((long long)a.ny * a.nz) / 2;
+  const bool ok = q < npairs;
+  const long long r0 = 2 * q * a.nx, r1 = r0 + a.nx;
+  typename X::B buf{sm + (size_t)l * X::B::SIZE};
+  cpx<T> v[X::R], w[X::R];
+  for (int g = 0; g < a.n_groups; ++g) {
+    const T* in = a.in[a.g_io[g]];
+#pragma unroll
+    for (int r = 0; r < X::R; ++r) {
+      const int xp = F::nat_pos(t, r);
+      v[r] = ok ? cmk(RK_LDG(in + r0 + xp) * mask_of<T>(a.in_mask, r0 + xp),
+                      RK_LDG(in + r1 + xp) * mask_of<T>(a.in_mask, r1 + xp))
+                : cmk((T)0, (T)0);
+    }
+    F::forward(v, t, buf, a.tw);
+    for (int qq = a.g_begin[g]; qq < a.g_begin[g + 1]; ++qq) {
+      const int m = a.term_m[qq];
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) w[r] = spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
+      F::inverse(w, t, buf, a.tw);
+      T* out = a.out[a.term_io[qq]];
+      if (ok)
+#pragma unroll
+        for (int r = 0; r < X::R; ++r) {
+          const int xp = F::nat_pos(t, r);
+          out[r0 + xp] = w[r].x * mask_of<T>(a.out_mask, r0 + xp);
+          out[r1 + xp] = w[r].y * mask_of<T>(a.out_mask, r1 + xp);
+        }
+    }
+  }
+}
+
+template <typename T, int N, int LX>
+__global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_merge(const PassArgs<T> a) {
+  using X = XPass<T, N, LX>;
+  using F = typename X::F;
+  RK_DYN_SMEM(cpx<T>, sm);
+  const int t = threadIdx.x % X::P, l = threadIdx.x / X::P;
+  const long long q = (long long)blockIdx.x * LX + l;
+  const long long npairs = ((long long)a.ny * a.nz) / 2;
+  const bool ok = q < npairs;
+  const long long r0 = 2 * q * a.nx, r1 = r0 + a.nx;
+  typename X::B buf{sm + (size_t)l * X::B::SIZE};
+  cpx<T> v[X::R], acc[X::R];
+  for (int g = 0; g < a.n_groups; ++g) {
+#pragma unroll
+    for (int r = 0; r < X::R; ++r) acc[r] = cmk((T)0, (T)0);
+    for (int qq = a.g_begin[g]; qq < a.g_begin[g + 1]; ++qq) {
+      const T* in = a.in[a.term_io[qq]];
+      const int m = a.term_m[qq];
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) {
+        const int xp = F::nat_pos(t, r);
+        v[r] = ok ? cmk(RK_LDG(in + r0 + xp), RK_LDG(in + r1 + xp)) : cmk((T)0, (T)0);
+      }
+      F::forward(v, t, buf, a.tw);
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) acc[r] = acc[r] + spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
+    }
+    F::inverse(acc, t, buf, a.tw);
+    T* out = a.out[a.g_io[g]];
+    if (ok)
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) {
+        const int xp = F::nat_pos(t, r);
+        out[r0 + xp] = acc[r].x * mask_of<T>(a.out_mask, r0 + xp);
+        out[r1 + xp] = acc[r].y * mask_of<T>(a.out_mask, r1 + xp);
+      }
+  }
+}
+
+// ------------------------------------------------------- fused z pass (Alg. 2-4)
+enum ZMode { Z_STIFF = 0, Z_EVAL_U = 1, Z_TRANSPOSE_U = 2 };
+
+template <typename T>
+struct ZArgs {
+  // groups of basis indices p sharing (alpha_x, alpha_y); terms carry alpha_z and p
+  int n_groups;
+  int g_begin[kMaxOut + 1];
+  int term_mz[kMaxOut];
+  int term_p[kMaxOut];
+  const T* in[kMaxIn];   // Z_STIFF, Z_EVAL_U: one field per group (after x, y passes)
+  T* out[kMaxIn];        // Z_STIFF, Z_TRANSPOSE_U: one field per group
+  const T* in1;          // Z_TRANSPOSE_U: the input field (y)
+  T* out1;               // Z_EVAL_U: the output field (u)
+  const T* b;            // coefficient fields [4][s][nbox]: b^0, b^x, b^y, b^z
+  int s;
+  const T* wfield;       // Z_STIFF: chi*V;  Z_TRANSPOSE_U: optional weight (chi*V for f^r)
+  const uint8_t* mask;   // Z_EVAL_U: output mask (chi);  Z_TRANSPOSE_U: optional weight (chi)
+  const T* coef;         // z-axis spectral multipliers
+  const cpx<T>* tw;      // z-axis twiddles
+  int nx, ny, nz;
+  long long nbox;
+};
+
+template <typename T, int N, int L, int MODE>
+struct ZPass {
+  using S = Strided<T, N, L>;
+  using F = typename S::F;
+  static constexpr int P = F::P, R = F::R;
+  static constexpr int THREADS = L * P;
+  static constexpr size_t SMEM_BUF = sizeof(cpx<T>) * (size_t)N * L;
+  static constexpr size_t SMEM = SMEM_BUF * (MODE == Z_STIFF ? 4 : 1);
+};
+
+template <typename T, int N, int L, int MODE>
+__global__ void __launch_bounds__(ZPass<T, N, L, MODE>::THREADS) k_z_fused(const ZArgs<T> a) {
+  using Z = ZPass<T, N, L, MODE>;
+  using S = typename Z::S;
+  using F = typename Z::F;
+  RK_DYN_SMEM(cpx<T>, sm);
+  const int l = threadIdx.x % L, t = threadIdx.x / L;
+  const int x = blockIdx.x * 2 * L + 2 * l;
+  const bool ok = x < a.nx;
+  const long long zs = (long long)a.nx * a.ny;  // line stride along z
+  const long long base = (long long)x + (long long)blockIdx.y * a.nx;
+  InterleavedBuf<T, F::N1, F::N2> buf{sm + l, L};
+  // per-thread accumulators A^x, A^y, A^z (Eq. 90) at the thread's own nodes
+  cpx<T>* Acc = sm + (size_t)N * L;
+  auto A = [&](int k, int r) -> cpx<T>& { return Acc[((size_t)k * N + F::nat_pos(t, r)) * L + l]; };
+  auto coef_pair = [&](int which, int p, long long off) -> cpx<T> {
+    return ok ? S::load(a.b + ((long long)which * a.s + p) * a.nbox, off) : cmk((T)0, (T)0);
+  };
+  cpx<T> v[Z::R], w[Z::R];
+
+  if (MODE == Z_STIFF || MODE == Z_EVAL_U) {
+    cpx<T> u[MODE == Z_EVAL_U ? Z::R : 1];
+    if (MODE == Z_STIFF) {
+#pragma unroll
+      for (int r = 0; r < Z::R; ++r) A(0, r) = A(1, r) = A(2, r) = cmk((T)0, (T)0);
+    } else {
+#pragma unroll
+      for (int r = 0; r < Z::R; ++r) u[r] = cmk((T)0, (T)0);
+    }
+    // forward chain: D_p = conv_z(E_{ax,ay}, T_{az})   (Alg. 2 loop 1, Alg. 3)
+    for (int g = 0; g < a.n_groups; ++g) {
+      const T* in = a.in[g];
+#pragma unroll
+      for (int r = 0; r < Z::R; ++r) v[r] = ok ? S::load(in, base + F::nat_pos(t, r) * zs) : cmk((T)0, (T)0);
+      F::forward(v, t, buf, a.tw);
+      for (int q = a.g_begin[g]; q < a.g_begin[g + 1]; ++q) {
+        const int mz = a.term_mz[q], p = a.term_p[q];
+#pragma unroll
+        for (int r = 0; r < Z::R; ++r) w[r] = spec_mul(v[r], a.coef, N, mz, F::spec_idx(t, r), 0);
+        F::inverse(w, t, buf, a.tw);
+#pragma unroll
+        for (int r = 0; r < Z::R; ++r) {
+          const long long off = base + F::nat_pos(t, r) * zs;
+          if (MODE == Z_STIFF) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              cpx<T> bk = coef_pair(1 + k, p, off);
+              cpx<T>& Ak = A(k, r);
+              Ak = cmk(Ak.x + bk.x * w[r].x, Ak.y + bk.y * w[r].y);
+            }
+          } else {
+            cpx<T> b0 = coef_pair(0, p, off);
+            u[r] = cmk(u[r].x + b0.x * w[r].x, u[r].y + b0.y * w[r].y);
+          }
+        }
+      }
+    }
+    if (MODE == Z_EVAL_U) {
+      if (ok)
+#pragma unroll
+        for (int r = 0; r < Z::R; ++r) {
+          const long long off = base + F::nat_pos(t, r) * zs;
+          T m0 = a.mask ? (T)a.mask[off] : (T)1, m1 = a.mask ? (T)a.mask[off + 1] : (T)1;
+          S::store(a.out1, off, cmk(u[r].x * m0, u[r].y * m1));
+        }
+      return;
+    }
+  }
+
+  // reflected chain: G_{ax,ay} = sum_az conv_z(g_p, Tbar_az)   (Alg. 2 loop 2, Alg. 4)
+  cpx<T> y[MODE == Z_TRANSPOSE_U ? Z::R : 1];
+  if (MODE == Z_TRANSPOSE_U) {
+#pragma unroll
+    for (int r = 0; r < Z::R; ++r) {
+      const long long off = base + F::nat_pos(t, r) * zs;
+      cpx<T> yv = ok ? S::load(a.in1, off) : cmk((T)0, (T)0);
+      if (ok && a.wfield) {
+        cpx<T> wv = S::load(a.wfield, off);
+        yv = cmk(yv.x * wv.x, yv.y * wv.y);
+      }
+      if (ok && a.mask) yv = cmk(yv.x * (T)a.mask[off], yv.y * (T)a.mask[off + 1]);
+      y[r] = yv;
+    }
+  }
+  for (int g = 0; g < a.n_groups; ++g) {
+    cpx<T> acc[Z::R];
+#pragma unroll
+    for (int r = 0; r < Z::R; ++r) acc[r] = cmk((T)0, (T)0);
+    for (int q = a.g_begin[g]; q < a.g_begin[g + 1]; ++q) {
+      const int mz = a.term_mz[q], p = a.term_p[q];
+#pragma unroll
+      for (int r = 0; r < Z::R; ++r) {
+        const long long off = base + F::nat_pos(t, r) * zs;
+        if (MODE == Z_STIFF) {
+          // g_p = chi V sum_k b^k_p A^k   (Eq. 91: C^k_p = chi V b^k_p)
+          cpx<T> cv = ok ? S::load(a.wfield, off) : cmk((T)0, (T)0);
+          cpx<T> s = cmk((T)0, (T)0);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            cpx<T> bk = coef_pair(1 + k, p, off);
+            cpx<T> Ak = A(k, r);
+            s = cmk(s.x + bk.x * Ak.x, s.y + bk.y * Ak.y);
+          }
+          v[r] = cmk(cv.x * s.x, cv.y * s.y);
+        } else {
+          // g_p = w b^0_p y   (Eq. 92 with w = chi V; its transpose use with w = chi)
+          cpx<T> b0 = coef_pair(0, p, off);
+          v[r] = cmk(b0.x * y[r].x, b0.y * y[r].y);
+        }
+      }
+      F::forward(v, t, buf, a.tw);
+#pragma unroll
+      for (int r = 0; r < Z::R; ++r) acc[r] = acc[r] + spec_mul(v[r], a.coef, N, mz, F::spec_idx(t, r), 1);
+    }
+    F::inverse(acc, t, buf, a.tw);
+    if (ok)
+#pragma unroll
+      for (int r = 0; r < Z::R; ++r) S::store(a.out[g], base + F::nat_pos(t, r) * zs, acc[r]);
+  }
+}
+
+}  // namespace rk

@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative L2 over the domain nodes, 0 required off the domain):
+  FP64 path   1e-10   (the FC-RKPM result is the traditional RKPM result up to
+                       rounding: Sec. 6.1, "identical up to the machine precision")
+  FP32 path   2e-6    (single-precision FFT convolutions: a few ulps of FP32,
+                       ~6e-8, times the O(log N) growth of the transforms and the
+                       two chained convolutions of Alg. 2; measured 2-5e-7)
+  mixed solve 1e-9 against the FP64 solution after FP64 refinement.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle, apply_K_sampled, b_sampled
+from paper_2403_19854_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2403_19854_gb300 import rk  # noqa: E402
+
+DEV = torch.device("cuda:0")
+TOL64 = 1e-10
+TOL32 = 2e-6
+
+
+def rel(a, b, m=None):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if m is not None:
+        a, b = a[m], b[m]
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def tdev(x, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(x), device=DEV)
+    return t.to(dtype) if dtype is not None else t
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+def _problem(kind, nb, a, deg, seed=11):
+    if kind == "cube":
+        return W.cube_problem(nb, a, deg, "sin")
+    if kind == "paper":
+        return W.cube_problem(nb, a, deg, "paper", -1.0, 1.0)
+    return W.spheres_problem(n_box=nb, n_spheres=3, a_tilde=a, degree=deg, r_range=(0.2, 0.3), seed=seed)
+
+
+CASES = [("cube", 16, 2.0, 1), ("cube", 16, 2.5, 1), ("cube", 16, 3.0, 2), ("spheres", 16, 2.5, 1),
+         ("spheres", 32, 3.0, 2), ("paper", 8, 1.5, 1), ("cube", 32, 3.5, 1)]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: f"{c[0]}{c[1]}-a{c[2]}-n{c[3]}")
+def case(request):
+    kind, nb, a, deg = request.param
+    p = _problem(kind, nb, a, deg)
+    H = rk.Handle.from_problem(p, device=DEV)
+    o = Oracle(p.n, p.h, a, deg, p.chi)
+    yield p, H, o
+    H.close()
+
+
+def test_setup_coefficients_alg1(case):
+    """b^0, b^x, b^y, b^z of Alg. 1 (FFT moments + per-node Cholesky) == oracle rows of
+    M^{-1} built from explicit neighbour sums, per coefficient family."""
+    p, H, o = case
+    m = p.chi > 0
+    bg = np_(H.get_b(torch.empty(4 * p.s * p.nbox, dtype=torch.float64, device=DEV)))
+    bo = o.b_fields()
+    for i in range(4):
+        assert rel(bg[i][:, m], bo[i][:, m]) < TOL64, f"b family {i}"
+    assert H.singular == (0, -1)
+
+
+def test_stiffness_action_fp64_alg2(case):
+    p, H, o = case
+    m = p.chi > 0
+    d = W.random_field(p.nbox, 3)
+    f = np_(H.apply_K(tdev(d)))
+    fo = o.apply_K(p.V, d * p.chi)
+    assert rel(f, fo, m) < TOL64
+    assert np.all(f[~m] == 0.0)
+
+
+def test_stiffness_action_fp32_alg2(case):
+    p, H, o = case
+    m = p.chi > 0
+    d = W.random_field(p.nbox, 4).astype(np.float32)
+    f = np_(H.apply_K(tdev(d))).astype(np.float64)
+    fo = o.apply_K(p.V, d.astype(np.float64) * p.chi)
+    assert rel(f, fo, m) < TOL32
+    assert np.all(f[~m] == 0.0)
+
+
+def test_rhs_alg4(case):
+    p, H, o = case
+    m = p.chi > 0
+    r = W.random_field(p.nbox, 5)
+    fr = np_(H.rhs(tdev(r)))
+    assert rel(fr, o.rhs(p.V, r * p.chi), m) < TOL64
+    assert np.all(fr[~m] == 0.0)
+
+
+def test_eval_u_alg3_and_transpose(case):
+    p, H, o = case
+    m = p.chi > 0
+    d = W.random_field(p.nbox, 6)
+    u = np_(H.eval_u(tdev(d)))
+    assert rel(u, o.eval_u(d * p.chi), m) < TOL64
+    w = np_(H.eval_u_transpose(tdev(d)))
+    assert rel(w, o.eval_u_transpose(d * p.chi), m) < TOL64
+    assert np.all(u[~m] == 0.0) and np.all(w[~m] == 0.0)
+
+
+def test_host_pointers_same_result(case):
+    """The ABI accepts host arrays (staged by the library) with the same result."""
+    p, H, o = case
+    d = W.random_field(p.nbox, 7)
+    f_host = H.apply_K(d)
+    f_dev = np_(H.apply_K(tdev(d)))
+    assert np.array_equal(f_host, f_dev)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nb,a", [(16, 2.0), (16, 2.5), (32, 2.0)])
+def test_solve_alg5_matches_oracle(nb, a, prec):
+    """Alg. 5 with strong Dirichlet data (random g on Gamma_g): d and u^h against the
+    oracle's direct / CG solve of the assembled system."""
+    p = W.cube_problem(nb, a, 1, "sin")
+    p.g = np.where(p.chi_gamma > 0, 0.1 * W.random_field(p.nbox, 5), 0.0)
+    H = rk.Handle.from_problem(p, device=DEV)
+    o = Oracle(p.n, p.h, a, 1, p.chi)
+    do, info_o = o.solve(p.V, p.chi_gamma, p.r, p.g, tol=1e-14)
+    uo = o.eval_u(do)
+    d, u, info = H.solve(tdev(p.r), tdev(p.g), precision=prec, tol=1e-13)
+    assert info["rel_residual"] <= 1e-13
+    assert rel(np_(d), do) < 1e-9
+    assert rel(np_(u), uo) < 1e-9
+    gam = p.chi_gamma > 0
+    assert np.array_equal(np_(d)[gam], p.g[gam])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_adjoint_matches_oracle_gradient(prec):
+    """dJ/dr and dJ/dg from the adjoint solve against the oracle's assembled-K gradient."""
+    p = W.adjoint_problem(n_box=16, a_tilde=2.5, degree=1, sigma=0.2)
+    H = rk.Handle.from_problem(p, device=DEV)
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    ut = p.meta["u_target"]
+    Jo, gro, ggo, _, _ = o.adjoint(p.V, p.chi, p.chi_gamma, p.r, p.g, ut)
+    J, gr, gg, info = H.solve_adjoint(tdev(p.r), tdev(p.g), tdev(ut), precision=prec, tol=1e-13)
+    assert abs(J - Jo) <= 1e-10 * Jo
+    assert rel(np_(gr), gro) < 1e-8
+    assert rel(np_(gg), ggo) < 1e-8
+
+
+@pytest.mark.parametrize("nb,a,deg", [(128, 2.5, 1), (96, 2.5, 1), (64, 3.0, 2)])
+def test_full_size_sampled_parity(nb, a, deg):
+    """At full sizes: K.u (FP64 and FP32) and b on sampled nodes, each recomputed by the
+    oracle from scratch; the sample includes faces, edges and corners of the cube."""
+    p = W.cube_problem(nb, a, deg, "sin")
+    H = rk.Handle.from_problem(p, device=DEV)
+    rng = np.random.default_rng(nb)
+    n_om = p.meta["n_omega_side"]
+    pts = [(0, 0, 0), (n_om - 1, 0, 0), (1, n_om - 1, 2), (n_om - 1, n_om - 1, n_om - 1), (n_om // 2,) * 3]
+    pts += [tuple(rng.integers(0, n_om, 3)) for _ in range(40)]
+    sample = np.array([i + nb * (j + nb * k) for i, j, k in pts], dtype=np.int64)
+    d = W.random_field(p.nbox, 9)
+    f64 = np_(H.apply_K(tdev(d)))
+    f32 = np_(H.apply_K(tdev(d.astype(np.float32)))).astype(np.float64)
+    fo = apply_K_sampled(p.n, p.h, a, deg, p.chi, p.V, d, sample)
+    assert rel(f64[sample], fo) < TOL64
+    fo32 = apply_K_sampled(p.n, p.h, a, deg, p.chi, p.V, d.astype(np.float32).astype(np.float64), sample)
+    assert rel(f32[sample], fo32) < 10 * TOL32
+    bg = np_(H.get_b(torch.empty(4 * p.s * p.nbox, dtype=torch.float64, device=DEV)))
+    bo = b_sampled(p.n, p.h, a, deg, p.chi, sample)
+    for i in range(4):
+        assert rel(bg[i][:, sample].T, bo[:, i, :]) < TOL64
+
+
+def test_gap_narrower_than_support_is_rejected():
+    """A domain that touches its periodic image within the support is refused (Eq. 66)."""
+    p = W.cube_problem(16, 2.0, 1, "sin")
+    chi = p.chi.reshape(16, 16, 16).copy()
+    chi[:, :, 15] = chi[:, :, 0]   # fill the gap on x
+    with pytest.raises(rk.RKError) as e:
+        rk.Handle(p.n, p.h, tdev(chi.reshape(-1)), tdev(p.chi_gamma), tdev(p.V), 1, 2.0)
+    assert e.value.status == 8
+
+
+def test_singular_moment_reported():
+    """An isolated node has too few neighbours for a linear basis (Eq. 5): reported,
+    not fatal."""
+    chi = np.zeros(16 ** 3, dtype=np.uint8)
+    chi[5 + 16 * (5 + 16 * 5)] = 1
+    V = chi * 1e-3
+    H = rk.Handle((16, 16, 16), (0.1, 0.1, 0.1), tdev(chi), tdev(np.zeros_like(chi)), tdev(V), 1, 2.0)
+    assert H.setup_status == 4
+    assert H.singular == (1, 5 + 16 * (5 + 16 * 5))
