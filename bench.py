@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""FC-RKPM benchmark: K.u throughput and time-to-solve of the 3D Poisson unit-cube
+problem (linear basis, a = 2.5h, manufactured solution sin(pi x) sin(pi y) sin(pi z))
+on a 256^3 periodic box (254^3 domain nodes).
+
+One step = the whole solve path on inputs resident in HBM: rk_setup (kernel tables,
+FP64 moment convolutions, per-node M^{-1} -> b; Alg. 1) + f^r (Alg. 4) + CG with FP32
+K.u inside FP64 iterative refinement (Alg. 2, 5) to the requested FP64 residual +
+u^h (Alg. 3).  value = domain DOF x K.u applications / second over the timed steps.
+
+Also reported: the same path through the C ABI with pinned host buffers (e2e), the
+plain FP64 GPU solve of the same problem (time-to-solve, iterations, agreement),
+isolated K.u rates, the dominant kernel's HBM roofline from live CUDA-event timing,
+and the FP64 oracle timed on the host (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank solves its own replica (independent problems, weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "K·u DOF/s and time-to-solve at 256³, FP32-mixed vs FP64 GPU at 1e-9 rel L2"
+UNIT = "DOF/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        loaded = [v for v in sm if mx and v > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------- oracle
+def oracle_kd_rate(n_box=64, a_tilde=2.5, reps=3):
+    """FP64 oracle matrix-free K.d (neighbour loops, one host core) on a bounded cube
+    sample; returns (DOF/s, sample description, seconds)."""
+    from oracle.oracle import Oracle
+    from paper_2403_19854_gb300 import workloads as W
+    p = W.cube_problem(n_box, a_tilde, 1, "sin")
+    t0 = time.perf_counter()
+    o = Oracle(p.n, p.h, a_tilde, 1, p.chi)
+    tb = time.perf_counter() - t0
+    d = W.random_field(p.nbox, 1) * p.chi
+    o.apply_K(p.V, d)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        o.apply_K(p.V, d)
+    dt = (time.perf_counter() - t0) / reps
+    desc = (f"oracle matrix-free K.d (FP64 neighbour loops, 1 thread) on the {n_box}^3-box unit cube "
+            f"({p.n_omega} DOF, a=2.5h, linear), mean of {reps} after 1 warm-up; shape-function build "
+            f"{tb:.1f} s excluded")
+    return p.n_omega / dt, desc, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    vals = []
+    desc = ""
+    t_all = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        v, desc, dt = oracle_kd_rate(reps=1)
+        if i >= args.warmup:
+            vals.append(v)
+    elapsed = time.perf_counter() - t_all
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / (args.warmup + args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cube256-linear-a2.5-sin (oracle on a bounded 64^3-box sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- our arm
+# Algorithmic bytes per box node of one launch of each pass kernel (s = 4, linear
+# basis; w = bytes per real).  x_split: d + chi mask in, 2 fields out; y_split: 2 in,
+# 3 out; z_stiff: 3 in + 3s coefficient fields + chi V in, 3 out; y_merge: 3 in, 2 out;
+# x_merge: 2 in + mask, 1 out.
+def pass_bytes(cls, w, s=4):
+    nx = 2
+    ny = 3
+    return {"x_split": 1 * w + 1 + nx * w, "y_split": (nx + ny) * w, "z_stiff": (ny + 3 * s + 1 + ny) * w,
+            "y_merge": (ny + nx) * w, "x_merge": nx * w + 1 + w}.get(cls)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2403_19854_gb300 import rk
+    from paper_2403_19854_gb300 import workloads as W
+
+    rk.lib()
+    p = W.cube_problem(args.size, 2.5, 1, "sin")
+    n_dof = p.n_omega
+    chi = torch.as_tensor(p.chi, device=dev)
+    cg = torch.as_tensor(p.chi_gamma, device=dev)
+    V = torch.as_tensor(p.V, device=dev)
+    r = torch.as_tensor(p.r, device=dev)
+    g = torch.as_tensor(p.g, device=dev)
+    d = torch.empty(p.nbox, dtype=torch.float64, device=dev)
+    u = torch.empty_like(d)
+    opts = rk.default_opts(precision="mixed", tol=args.tol)
+    stream = torch.cuda.current_stream()
+
+    def step(prof=False):
+        H = rk.Handle(p.n, p.h, chi, cg, V, 1, 2.5)
+        if prof:
+            H.profile(True)
+        _, _, info = H.solve(r, g, d, u, opts=opts)
+        pr = H.profile_read() if prof else None
+        H.close()
+        return info, pr
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    clk = Clocks(local)
+    barrier()
+    clk.start()
+    L0 = rk.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos, profs = [], []
+    for _ in range(args.steps):
+        info, pr = step(prof=True)
+        infos.append(info)
+        profs.append(pr)
+    e1.record(stream)
+    barrier()
+    L1 = rk.kernel_launches()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    matvecs = sum(i["matvec_f32"] + i["matvec_f64"] for i in infos)
+    value = world * n_dof * matvecs / (ms / 1e3)
+    u_mixed = u.cpu().numpy().copy()
+
+    # kernel profile over the timed steps: dominant class and its roofline
+    agg = {}
+    for pr in profs:
+        for k, (t_ms, n) in pr.items():
+            a = agg.setdefault(k, [0.0, 0])
+            a[0] += t_ms
+            a[1] += n
+    tot = sum(v[0] for v in agg.values())
+    dom = max(agg.items(), key=lambda kv: kv[1][0])
+    (dname, dprec), (dms, dn) = dom
+    w = 8 if dprec == "f64" else 4
+    peak, peak_kind = _peaks()
+    bpn = pass_bytes(dname, w)
+    roofline = None
+    if bpn is not None:
+        traffic = args.traffic_bytes if args.traffic_bytes > 0 else None
+        per_launch = bpn * p.nbox
+        achieved = per_launch / (dms / dn / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"{dname}_{dprec}", "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                    "algorithmic_bytes_per_launch": per_launch, "peak_source": peak_kind,
+                    "share_of_step_kernel_time": dms / tot}
+    profile_summary = {f"{k[0]}_{k[1]}": {"ms_total": v[0], "launches": v[1], "share": v[0] / tot}
+                       for k, v in sorted(agg.items(), key=lambda kv: -kv[1][0])}
+
+    # isolated K.u rates (resident d, f)
+    H = rk.Handle(p.n, p.h, chi, cg, V, 1, 2.5)
+    kd = {}
+    for dt_name, tdt in (("f32", torch.float32), ("f64", torch.float64)):
+        x = torch.rand(p.nbox, dtype=tdt, device=dev)
+        y = torch.empty_like(x)
+        reps = 20 if tdt == torch.float32 else 5
+        for _ in range(3):
+            H.apply_K(x, y)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            H.apply_K(x, y)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t_ku = a0.elapsed_time(a1) / reps
+        kd[dt_name] = {"ms": t_ku, "dof_per_s": n_dof / (t_ku / 1e3)}
+    H.close()
+
+    # plain FP64 GPU solve of the same problem, and agreement with the mixed solution
+    fp64 = None
+    if args.fp64_ref:
+        H = rk.Handle(p.n, p.h, chi, cg, V, 1, 2.5)
+        d64 = torch.empty_like(d)
+        u64 = torch.empty_like(d)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, i64 = H.solve(r, g, d64, u64, opts=rk.default_opts(precision="fp64", tol=args.tol),
+                             raise_on_error=False)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        H.close()
+        u64n = u64.cpu().numpy()
+        m = p.chi > 0
+        diff = float(np.linalg.norm((u_mixed - u64n)[m]) / np.linalg.norm(u64n[m]))
+        err_exact = float(np.linalg.norm((u64n - p.u_exact)[m]) / np.linalg.norm(p.u_exact[m]))
+        fp64 = {"time_to_solve_s": t64, "iterations": i64["iterations"], "matvec_f64": i64["matvec_f64"],
+                "rel_residual": i64["rel_residual"], "status": i64["status"],
+                "rel_l2_u_mixed_vs_fp64": diff, "rel_l2_u_fp64_vs_exact": err_exact}
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timing)
+    hp = {k: torch.as_tensor(getattr(p, k)).pin_memory() for k in ("chi", "chi_gamma", "V", "r", "g")}
+    hd = torch.empty(p.nbox, dtype=torch.float64).pin_memory()
+    hu = torch.empty(p.nbox, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    e2e_mv = 0
+    for i in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H = rk.Handle(p.n, p.h, hp["chi"], hp["chi_gamma"], hp["V"], 1, 2.5, stream=rk.ctypes.c_void_p(stream.cuda_stream))
+        _, _, ie = H.solve(hp["r"], hp["g"], hd, hu, opts=opts, stream=rk.ctypes.c_void_p(stream.cuda_stream))
+        H.close()
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_mv += ie["matvec_f32"] + ie["matvec_f64"]
+    e2e_value = n_dof * e2e_mv / (sum(e2e_ms) / 1e3) * world
+    h2d = p.nbox * (1 + 1 + 8 + 8 + 8)
+    d2h = p.nbox * (8 + 8)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, desc, _ = oracle_kd_rate()
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        m = p.chi > 0
+        err = float(np.linalg.norm((u_mixed - p.u_exact)[m]) / np.linalg.norm(p.u_exact[m]))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"cube{args.size}-linear-a2.5-sin", "box": list(p.n), "n_omega": n_dof,
+                       "degree": 1, "a_tilde": 2.5, "precision": "mixed (FP32 K.u, FP64 dots/refinement)",
+                       "tol": args.tol, "l2": "inputs and working set larger than L2 (no flush needed)",
+                       "parallelism": f"replicas x{world}"},
+            "time_to_solve_s": {"mixed": ms / args.steps / 1e3, "fp64": fp64["time_to_solve_s"] if fp64 else None},
+            "solve": {"iterations": infos[-1]["iterations"], "outer": infos[-1]["outer"],
+                      "matvec_f32": infos[-1]["matvec_f32"], "matvec_f64": infos[-1]["matvec_f64"],
+                      "rel_residual": infos[-1]["rel_residual"], "rel_l2_u_vs_exact": err},
+            "fp64_solve": fp64,
+            "kU_isolated": kd,
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": statistics.mean(e2e_ms)},
+            "gpu_launches": int(L1 - L0),
+            "roofline": roofline,
+            "kernel_profile": profile_summary,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--fp64-ref", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic-bytes", type=float, default=0.0,
+                    help="ncu dram bytes per launch of the dominant kernel (from profiles/), if measured")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -182,6 +182,39 @@ rk_status rk_solve_adjoint(rk_handle* h, const double* r, const double* g, const
                            double* dJ_dr, double* dJ_dg, double* J, const rk_solve_opts* opts,
                            rk_solve_info* info, void* stream);
 
+/* ---- instrumentation ---------------------------------------------------- */
+
+/* Kernel classes timed by rk_profile_read. */
+enum {
+  RK_PROF_X_SPLIT = 0,       /* x pass, forward chain (and set-up moments) */
+  RK_PROF_Y_SPLIT = 1,       /* y pass, forward chain */
+  RK_PROF_Z_SPLIT = 2,       /* z pass of the set-up moments */
+  RK_PROF_Z_STIFF = 3,       /* fused z pass of Alg. 2 */
+  RK_PROF_Z_EVAL_U = 4,      /* fused z pass of Alg. 3 */
+  RK_PROF_Z_TRANSPOSE_U = 5, /* fused z pass of Alg. 4 / transpose of Alg. 3 */
+  RK_PROF_Y_MERGE = 6,       /* y pass, reflected chain */
+  RK_PROF_X_MERGE = 7,       /* x pass, reflected chain */
+  RK_PROF_MOMENT_SOLVE = 8,  /* per-node M^{-1} of Alg. 1 */
+  RK_PROF_CG_VECTOR = 9,     /* CG dot products and vector updates (per iteration) */
+  RK_PROF_CLASSES = 10
+};
+
+/* Total number of kernels this library has launched in the process. */
+int64_t rk_kernel_launches(void);
+
+/* Start (enable = 1) or stop (0) timing every kernel class of this handle with
+ * CUDA events recorded on the launching stream; counters are cleared. */
+rk_status rk_profile_enable(rk_handle* h, int32_t enable);
+
+/* Accumulated milliseconds and launch counts per class since rk_profile_enable,
+ * entry c for the FP32 kernels of class c and entry RK_PROF_CLASSES + c for the
+ * FP64 ones (arrays of n_classes <= 2*RK_PROF_CLASSES entries, either may be
+ * NULL).  Waits for the recorded events. */
+rk_status rk_profile_read(rk_handle* h, double* ms, int64_t* launches, int32_t n_classes);
+
+/* Name of a kernel class ("" if out of range). */
+const char* rk_profile_class_name(int32_t cls);
+
 /* Release the handle and everything it owns (NULL is accepted). */
 rk_status rk_destroy(rk_handle* h);
 

@@ -145,6 +145,16 @@ struct rk_handle {
   unsigned long long* counters = nullptr;  // singular count, first singular
   long long n_singular = 0, first_singular = -1;
   std::vector<void*> owned;
+  // per-class kernel timing with CUDA events (rk_profile_enable)
+  struct Pend {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<Pend> pend;
+  double prof_ms[2 * RK_PROF_CLASSES] = {};  // [FP32 classes | FP64 classes]
+  long long prof_n[2 * RK_PROF_CLASSES] = {};
 
   template <typename T>
   rk_status alloc(T** p, size_t count) {
@@ -166,6 +176,61 @@ template <>
 float* rk_handle::ws<float>(int i) { return ws32 + (size_t)i * nbox; }
 
 namespace {
+
+cudaEvent_t prof_event(rk_handle* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Resolve the recorded event pairs into per-class milliseconds.
+void prof_flush(rk_handle* h) {
+  for (auto& p : h->pend) {
+    cudaEventSynchronize(p.b);
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      h->prof_ms[p.cls] += ms;
+      h->prof_n[p.cls] += 1;
+    }
+    h->ev_pool.push_back(p.a);
+    h->ev_pool.push_back(p.b);
+  }
+  h->pend.clear();
+}
+
+// Times the launches issued during its lifetime on stream s when profiling is on.
+struct ProfScope {
+  rk_handle* h;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(rk_handle* h_, int cls_, cudaStream_t s_) : h(h_), cls(cls_), s(s_) {
+    if (h->prof_on) {
+      a = prof_event(h);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = prof_event(h);
+    cudaEventRecord(b, s);
+    h->pend.push_back({cls, a, b});
+    if (h->pend.size() >= 2048) prof_flush(h);
+  }
+};
+
+template <typename T>
+constexpr int prof_cls(int c) {
+  return c + (sizeof(T) == 8 ? RK_PROF_CLASSES : 0);
+}
+
+const char* const kProfNames[RK_PROF_CLASSES] = {"x_split", "y_split", "z_split", "z_stiff", "z_eval_u",
+                                                 "z_transpose_u", "y_merge", "x_merge", "moment_solve", "cg_vector"};
 
 template <typename T>
 const T* coef_of(const rk_handle* h, int axis);
@@ -212,12 +277,14 @@ PassArgs<T> pass_base(const rk_handle* h, int axis) {
 }
 
 template <typename T>
-rk_status run_split(const rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s) {
+rk_status run_split(rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s) {
+  ProfScope ps(h, prof_cls<T>(axis == 0 ? RK_PROF_X_SPLIT : (axis == 1 ? RK_PROF_Y_SPLIT : RK_PROF_Z_SPLIT)), s);
   cudaError_t e = launch_split<T>(axis, h->n[axis], a, s);
   return e == cudaSuccess ? RK_OK : cuda_fail(e, "split pass");
 }
 template <typename T>
-rk_status run_merge(const rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s) {
+rk_status run_merge(rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s) {
+  ProfScope ps(h, prof_cls<T>(axis == 0 ? RK_PROF_X_MERGE : RK_PROF_Y_MERGE), s);
   cudaError_t e = launch_merge<T>(axis, h->n[axis], a, s);
   return e == cudaSuccess ? RK_OK : cuda_fail(e, "merge pass");
 }
@@ -328,7 +395,8 @@ ZArgs<T> z_base(const rk_handle* h) {
 }
 
 template <typename T>
-rk_status run_z(const rk_handle* h, int mode, const ZArgs<T>& a, cudaStream_t s) {
+rk_status run_z(rk_handle* h, int mode, const ZArgs<T>& a, cudaStream_t s) {
+  ProfScope ps(h, prof_cls<T>(mode == Z_STIFF ? RK_PROF_Z_STIFF : (mode == Z_EVAL_U ? RK_PROF_Z_EVAL_U : RK_PROF_Z_TRANSPOSE_U)), s);
   cudaError_t e = launch_z<T>(mode, h->n[2], a, s);
   return e == cudaSuccess ? RK_OK : cuda_fail(e, "z pass");
 }
@@ -544,11 +612,14 @@ rk_status cg_run(rk_handle* h, T* x, T* r, T* p, T* Ap, double rr_target, int ma
     }
     RK_TRY(op_K<T>(h, p, Ap, h->chi_omega, h->chi_omega, s));
     ++*matvecs;
-    RK_CK(launch_dot<T, T>(p, Ap, n, h->partials, h->dscal, s));
-    RK_CK(launch_cg_alpha(h->partials, h->cg, s));
-    RK_CK(launch_cg_xr<T>(x, r, p, Ap, h->cg, n, h->partials, s));
-    RK_CK(launch_cg_beta(h->partials, h->cg, s));
-    RK_CK(launch_cg_p<T>(p, r, h->cg, n, s));
+    {
+      ProfScope ps(h, prof_cls<T>(RK_PROF_CG_VECTOR), s);
+      RK_CK(launch_dot<T, T>(p, Ap, n, h->partials, h->dscal, s));
+      RK_CK(launch_cg_alpha(h->partials, h->cg, s));
+      RK_CK(launch_cg_xr<T>(x, r, p, Ap, h->cg, n, h->partials, s));
+      RK_CK(launch_cg_beta(h->partials, h->cg, s));
+      RK_CK(launch_cg_p<T>(p, r, h->cg, n, s));
+    }
     ++it;
   }
   *iters = it;
@@ -708,10 +779,39 @@ const char* rk_last_error_message(void) { return g_err.c_str(); }
 
 rk_status rk_destroy(rk_handle* h) {
   if (!h) return RK_OK;
+  prof_flush(h);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   for (void* p : h->owned) cudaFree(p);
   if (h->hscal) cudaFreeHost(h->hscal);
   delete h;
   return RK_OK;
+}
+
+int64_t rk_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+rk_status rk_profile_enable(rk_handle* h, int32_t enable) {
+  if (!h) return fail(RK_ERR_INVALID_ARG, "handle is NULL");
+  prof_flush(h);
+  for (int c = 0; c < 2 * RK_PROF_CLASSES; ++c) {
+    h->prof_ms[c] = 0.0;
+    h->prof_n[c] = 0;
+  }
+  h->prof_on = enable != 0;
+  return RK_OK;
+}
+
+rk_status rk_profile_read(rk_handle* h, double* ms, int64_t* launches, int32_t n_classes) {
+  if (!h || n_classes < 0) return fail(RK_ERR_INVALID_ARG, "bad arguments");
+  prof_flush(h);
+  for (int c = 0; c < n_classes && c < 2 * RK_PROF_CLASSES; ++c) {
+    if (ms) ms[c] = h->prof_ms[c];
+    if (launches) launches[c] = h->prof_n[c];
+  }
+  return RK_OK;
+}
+
+const char* rk_profile_class_name(int32_t cls) {
+  return (cls >= 0 && cls < RK_PROF_CLASSES) ? kProfNames[cls] : "";
 }
 
 rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_gamma, const double* V,
@@ -889,7 +989,10 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
     ma.first_singular = h->counters + 1;
     unsigned long long init[2] = {0ull, ~0ull};
     RK_CK(cudaMemcpyAsync(h->counters, init, sizeof(init), cudaMemcpyHostToDevice, s));
-    RK_CK(launch_moment_solve(ma, s));
+    {
+      ProfScope ps(h, prof_cls<double>(RK_PROF_MOMENT_SOLVE), s);
+      RK_CK(launch_moment_solve(ma, s));
+    }
     unsigned long long res[2];
     RK_CK(cudaMemcpyAsync(res, h->counters, sizeof(res), cudaMemcpyDeviceToHost, s));
     RK_CK(cudaStreamSynchronize(s));

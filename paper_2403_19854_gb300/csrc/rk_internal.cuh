@@ -4,9 +4,15 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "rk_passes.cuh"
 
 namespace rk {
+
+// Number of kernels launched by the library in this process.
+extern std::atomic<long long> g_launches;
+inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // Line lengths with instantiated FFT kernels.
 bool supported_length(int n);

@@ -39,6 +39,7 @@ cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
     auto k = k_x_split<T, N, LX>;
     cudaError_t e = set_smem(k, X::SMEM);
     if (e != cudaSuccess) return e;
+    count_launch();
     k<<<nb, X::THREADS, X::SMEM, s>>>(a);
   } else {
     constexpr int L = Cfg<T>::L;
@@ -47,6 +48,7 @@ cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
     auto k = k_strided_split<T, N, L>;
     cudaError_t e = set_smem(k, S::SMEM);
     if (e != cudaSuccess) return e;
+    count_launch();
     k<<<grid, S::THREADS, S::SMEM, s>>>(a);
   }
   return cudaGetLastError();
@@ -62,6 +64,7 @@ cudaError_t merge_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
     auto k = k_x_merge<T, N, LX>;
     cudaError_t e = set_smem(k, X::SMEM);
     if (e != cudaSuccess) return e;
+    count_launch();
     k<<<nb, X::THREADS, X::SMEM, s>>>(a);
   } else {
     constexpr int L = Cfg<T>::L;
@@ -70,6 +73,7 @@ cudaError_t merge_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
     auto k = k_strided_merge<T, N, L>;
     cudaError_t e = set_smem(k, S::SMEM);
     if (e != cudaSuccess) return e;
+    count_launch();
     k<<<grid, S::THREADS, S::SMEM, s>>>(a);
   }
   return cudaGetLastError();
@@ -83,6 +87,7 @@ cudaError_t z_n_mode(const ZArgs<T>& a, cudaStream_t s) {
   auto k = k_z_fused<T, N, L, MODE>;
   cudaError_t e = set_smem(k, Z::SMEM);
   if (e != cudaSuccess) return e;
+  count_launch();
   k<<<grid, Z::THREADS, Z::SMEM, s>>>(a);
   return cudaGetLastError();
 }

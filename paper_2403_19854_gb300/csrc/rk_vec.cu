@@ -5,6 +5,8 @@
 
 namespace rk {
 
+std::atomic<long long> g_launches{0};
+
 bool supported_length(int n) {
   switch (n) {
     case 8: case 16: case 32: case 64: case 96: case 128: case 256: return true;
@@ -15,6 +17,7 @@ bool supported_length(int n) {
 cudaError_t launch_moment_solve(const MomentArgs& a, cudaStream_t s) {
   const long long nb = (a.nbox + 127) / 128;
   const unsigned grid = (unsigned)(nb < 152 * 64 ? nb : 152 * 64);
+  count_launch();
   k_moment_solve<<<grid, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -65,7 +68,9 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_to(const double* part, d
 
 template <typename Ta, typename Tb>
 cudaError_t launch_dot(const Ta* a, const Tb* b, long long n, double* partials, double* out, cudaStream_t s) {
+  count_launch();
   k_dot<Ta, Tb><<<kRedBlocks, kRedThreads, 0, s>>>(a, b, n, partials);
+  count_launch();
   k_reduce_to<<<1, kRedThreads, 0, s>>>(partials, out);
   return cudaGetLastError();
 }
@@ -83,6 +88,7 @@ __global__ void k_cg_init(const double* part, CGState* st) {
   }
 }
 cudaError_t launch_cg_init(const double* partials, CGState* st, cudaStream_t s) {
+  count_launch();
   k_cg_init<<<1, kRedThreads, 0, s>>>(partials, st);
   return cudaGetLastError();
 }
@@ -103,6 +109,7 @@ __global__ void k_cg_alpha(const double* part, CGState* st) {
   }
 }
 cudaError_t launch_cg_alpha(const double* partials, CGState* st, cudaStream_t s) {
+  count_launch();
   k_cg_alpha<<<1, kRedThreads, 0, s>>>(partials, st);
   return cudaGetLastError();
 }
@@ -126,6 +133,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr(T* __restrict__ x, T* __r
 template <typename T>
 cudaError_t launch_cg_xr(T* x, T* r, const T* p, const T* Ap, CGState* st, long long n, double* partials,
                          cudaStream_t s) {
+  count_launch();
   k_cg_xr<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, Ap, st, n, partials);
   return cudaGetLastError();
 }
@@ -144,6 +152,7 @@ __global__ void k_cg_beta(const double* part, CGState* st) {
   }
 }
 cudaError_t launch_cg_beta(const double* partials, CGState* st, cudaStream_t s) {
+  count_launch();
   k_cg_beta<<<1, kRedThreads, 0, s>>>(partials, st);
   return cudaGetLastError();
 }
@@ -157,6 +166,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_p(T* __restrict__ p, const T
 }
 template <typename T>
 cudaError_t launch_cg_p(T* p, const T* r, const CGState* st, long long n, cudaStream_t s) {
+  count_launch();
   k_cg_p<T><<<kRedBlocks, kRedThreads, 0, s>>>(p, r, st, n);
   return cudaGetLastError();
 }
@@ -177,6 +187,7 @@ __global__ void k_dirichlet_d0(double* d0, const double* g, const uint8_t* cg, l
   RK_GRID_LOOP(i, n) d0[i] = cg[i] ? g[i] : 0.0;
 }
 cudaError_t launch_dirichlet_d0(double* d0, const double* g, const uint8_t* chi_gamma, long long n, cudaStream_t s) {
+  count_launch();
   k_dirichlet_d0<<<ew_grid(n), 256, 0, s>>>(d0, g, chi_gamma, n);
   return cudaGetLastError();
 }
@@ -186,6 +197,7 @@ __global__ void k_masked_diff(double* F, const double* a, const double* b, const
 }
 cudaError_t launch_masked_diff(double* F, const double* a, const double* b, const uint8_t* mask, long long n,
                                cudaStream_t s) {
+  count_launch();
   k_masked_diff<<<ew_grid(n), 256, 0, s>>>(F, a, b, mask, n);
   return cudaGetLastError();
 }
@@ -194,6 +206,7 @@ __global__ void k_to_f32(float* y, const double* x, double sc, long long n) {
   RK_GRID_LOOP(i, n) y[i] = (float)(x[i] * sc);
 }
 cudaError_t launch_to_f32(float* y, const double* x, double scale, long long n, cudaStream_t s) {
+  count_launch();
   k_to_f32<<<ew_grid(n), 256, 0, s>>>(y, x, scale, n);
   return cudaGetLastError();
 }
@@ -202,6 +215,7 @@ __global__ void k_acc_f32(double* x, const float* c, double sc, long long n) {
   RK_GRID_LOOP(i, n) x[i] += sc * (double)c[i];
 }
 cudaError_t launch_acc_f32(double* x, const float* c, double scale, long long n, cudaStream_t s) {
+  count_launch();
   k_acc_f32<<<ew_grid(n), 256, 0, s>>>(x, c, scale, n);
   return cudaGetLastError();
 }
@@ -210,6 +224,7 @@ __global__ void k_add(double* d, const double* a, const double* b, long long n) 
   RK_GRID_LOOP(i, n) d[i] = a[i] + b[i];
 }
 cudaError_t launch_add(double* d, const double* a, const double* b, long long n, cudaStream_t s) {
+  count_launch();
   k_add<<<ew_grid(n), 256, 0, s>>>(d, a, b, n);
   return cudaGetLastError();
 }
@@ -218,6 +233,7 @@ __global__ void k_sub(double* d, const double* a, const double* b, long long n) 
   RK_GRID_LOOP(i, n) d[i] = a[i] - b[i];
 }
 cudaError_t launch_sub(double* out, const double* a, const double* b, long long n, cudaStream_t s) {
+  count_launch();
   k_sub<<<ew_grid(n), 256, 0, s>>>(out, a, b, n);
   return cudaGetLastError();
 }
@@ -226,6 +242,7 @@ __global__ void k_mask(double* o, const double* a, const uint8_t* m, long long n
   RK_GRID_LOOP(i, n) o[i] = m[i] ? a[i] : 0.0;
 }
 cudaError_t launch_mask(double* out, const double* a, const uint8_t* mask, long long n, cudaStream_t s) {
+  count_launch();
   k_mask<<<ew_grid(n), 256, 0, s>>>(out, a, mask, n);
   return cudaGetLastError();
 }
@@ -234,6 +251,7 @@ __global__ void k_mul(double* a, const double* b, long long n) {
   RK_GRID_LOOP(i, n) a[i] *= b[i];
 }
 cudaError_t launch_mul(double* a, const double* b, long long n, cudaStream_t s) {
+  count_launch();
   k_mul<<<ew_grid(n), 256, 0, s>>>(a, b, n);
   return cudaGetLastError();
 }
@@ -242,6 +260,7 @@ __global__ void k_u8_to_f64(double* o, const uint8_t* m, long long n) {
   RK_GRID_LOOP(i, n) o[i] = m[i] ? 1.0 : 0.0;
 }
 cudaError_t launch_u8_to_f64(double* out, const uint8_t* m, long long n, cudaStream_t s) {
+  count_launch();
   k_u8_to_f64<<<ew_grid(n), 256, 0, s>>>(out, m, n);
   return cudaGetLastError();
 }
@@ -252,6 +271,7 @@ __global__ void k_fill(T* p, T v, long long n) {
 }
 template <typename T>
 cudaError_t launch_fill(T* p, T v, long long n, cudaStream_t s) {
+  count_launch();
   k_fill<T><<<ew_grid(n), 256, 0, s>>>(p, v, n);
   return cudaGetLastError();
 }
@@ -264,6 +284,7 @@ __global__ void k_copy(T* d, const T* s, long long n) {
 }
 template <typename T>
 cudaError_t launch_copy(T* dst, const T* src, long long n, cudaStream_t s) {
+  count_launch();
   k_copy<T><<<ew_grid(n), 256, 0, s>>>(dst, src, n);
   return cudaGetLastError();
 }

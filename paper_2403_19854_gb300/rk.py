@@ -25,7 +25,9 @@ RK_PREC_FP64, RK_PREC_MIXED = 0, 1
 
 EXPORTED = ["rk_default_solve_opts", "rk_supported_length", "rk_setup", "rk_singular_nodes", "rk_apply_K",
             "rk_rhs", "rk_eval_u", "rk_eval_u_transpose", "rk_get_b", "rk_get_shape", "rk_solve",
-            "rk_solve_adjoint", "rk_destroy", "rk_status_string", "rk_last_error_message"]
+            "rk_solve_adjoint", "rk_destroy", "rk_status_string", "rk_last_error_message",
+            "rk_kernel_launches", "rk_profile_enable", "rk_profile_read", "rk_profile_class_name"]
+PROF_CLASSES = 10
 
 
 class RKError(RuntimeError):
@@ -83,6 +85,12 @@ def lib():
     L.rk_status_string.restype = ctypes.c_char_p
     L.rk_last_error_message.argtypes = []
     L.rk_last_error_message.restype = ctypes.c_char_p
+    L.rk_kernel_launches.argtypes = []
+    L.rk_kernel_launches.restype = ctypes.c_int64
+    L.rk_profile_enable.argtypes = [vp, i32]
+    L.rk_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]
+    L.rk_profile_class_name.argtypes = [i32]
+    L.rk_profile_class_name.restype = ctypes.c_char_p
     for name in EXPORTED:
         if getattr(L, name).restype is ctypes.c_int:  # default
             pass
@@ -141,6 +149,11 @@ def default_opts(**kw) -> SolveOpts:
 
 def supported_length(n: int) -> bool:
     return bool(lib().rk_supported_length(int(n)))
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().rk_kernel_launches())
 
 
 class Handle:
@@ -241,6 +254,24 @@ class Handle:
         nom = ctypes.c_int64()
         _check(lib().rk_get_shape(self._h, ctypes.byref(n), ctypes.byref(s), ctypes.byref(nom)))
         return tuple(n), s.value, nom.value
+
+    # ---------------------------------------------------------- instrumentation
+    def profile(self, enable=True):
+        """Start/stop per-kernel-class CUDA-event timing (counters cleared)."""
+        _check(lib().rk_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{(class name, 'f32'|'f64'): (ms, launches)} since profile(True)."""
+        n = 2 * PROF_CLASSES
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        _check(lib().rk_profile_read(self._h, ms, cnt, n))
+        out = {}
+        for i in range(n):
+            if cnt[i]:
+                name = lib().rk_profile_class_name(i % PROF_CLASSES).decode()
+                out[(name, "f64" if i >= PROF_CLASSES else "f32")] = (ms[i], cnt[i])
+        return out
 
     # ------------------------------------------------------------------ solves
     def solve(self, r, g=None, d=None, u=None, opts=None, want_u=True, stream=None, raise_on_error=True, **kw):

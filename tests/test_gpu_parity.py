@@ -185,10 +185,13 @@ def test_full_size_sampled_parity(nb, a, deg):
 
 
 def test_gap_narrower_than_support_is_rejected():
-    """A domain that touches its periodic image within the support is refused (Eq. 66)."""
+    """A domain that touches its periodic image within the support is refused (Eq. 66).
+    At a = 2h the reach is one node (phi(2h) = 0), so one empty node suffices; with
+    no empty node along x the set-up must fail."""
     p = W.cube_problem(16, 2.0, 1, "sin")
     chi = p.chi.reshape(16, 16, 16).copy()
-    chi[:, :, 15] = chi[:, :, 0]   # fill the gap on x
+    chi[:, :, 14] = chi[:, :, 0]   # close the gap on x: nodes 13 and 0 become neighbours
+    chi[:, :, 15] = chi[:, :, 0]   # through the periodic boundary
     with pytest.raises(rk.RKError) as e:
         rk.Handle(p.n, p.h, tdev(chi.reshape(-1)), tdev(p.chi_gamma), tdev(p.V), 1, 2.0)
     assert e.value.status == 8
