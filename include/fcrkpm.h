@@ -215,6 +215,35 @@ rk_status rk_profile_read(rk_handle* h, double* ms, int64_t* launches, int32_t n
 /* Name of a kernel class ("" if out of range). */
 const char* rk_profile_class_name(int32_t cls);
 
+/*
+ * rk_apply_K_noalloc -- f = K d (the FP64 result of rk_apply_K) without allocating
+ * any memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory -- code running inside a host application
+ * that owns all device memory through its own pool, or latency-critical loops in
+ * which a cudaMalloc/cudaFree (which may synchronise the device) is not allowed.
+ * The caller passes every input and the output; the intermediate fields and the
+ * per-axis tables live in one fixed device array of RK_NOALLOC_MAX_DOUBLES doubles
+ * (about 16.8 MB) that every GPU loading this library holds until the process
+ * exits.
+ *   grid, degree, a_tilde  as for rk_setup (the same built box sides)
+ *   chi   uint8[nbox]  device, Eq. 40 (input and output mask)
+ *   chiV  double[nbox] device, chi o V
+ *   b     double[4*s*nbox] device, the coefficients in the layout of rk_get_b
+ *   d, f  double[nbox] device, input and output
+ * Limit: (n+1 + 2*n_Y) * nbox + 8192 <= RK_NOALLOC_MAX_DOUBLES with n_Y = 3 (degree
+ * 1) or 6 (degree 2): up to a 64^3 box for degree 1, 32^3 for degree 2; larger
+ * boxes return RK_ERR_UNSUPPORTED before any device work.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array and overwrite it (every
+ * value is written before it is read within a call), so calls whose GPU work
+ * overlaps -- on different streams or host threads -- race and must be ordered
+ * by the caller.
+ */
+#define RK_NOALLOC_MAX_DOUBLES 2105344LL
+rk_status rk_apply_K_noalloc(const rk_grid* grid, int32_t degree, double a_tilde, const uint8_t* chi,
+                             const double* chiV, const double* b, const double* d, double* f, void* stream);
+
 /* Release the handle and everything it owns (NULL is accepted). */
 rk_status rk_destroy(rk_handle* h);
 

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfcrkpm.so")
 
-SOURCES = ["rk_api.cu", "rk_vec.cu", "rk_pass_f32.cu", "rk_pass_f64.cu", "rk_z_f32.cu", "rk_z_f64.cu"]
+SOURCES = ["rk_api.cu", "rk_vec.cu", "rk_noalloc.cu", "rk_pass_f32.cu", "rk_pass_f64.cu", "rk_z_f32.cu", "rk_z_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "--expt-relaxed-constexpr", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,
          "-I", CSRC] + ARCH
