@@ -152,15 +152,19 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------- our arm
-# Algorithmic bytes per box node of one launch of each pass kernel (s = 4, linear
-# basis; w = bytes per real).  x_split: d + chi mask in, 2 fields out; y_split: 2 in,
-# 3 out; z_stiff: 3 in + 3s coefficient fields + chi V in, 3 out; y_merge: 3 in, 2 out;
-# x_merge: 2 in + mask, 1 out.
+# Algorithmic bytes per box node of one launch of each kernel class inside the CG
+# iteration (linear basis s = 4, w = bytes per real, u8 masks, int32 node index):
+#   x_split       p_old, r in; p, 2 fields out  (direction update fused, no input mask)
+#   y_split       2 in, 3 out
+#   z_split       3 in, s out
+#   stiff_pointwise  s in, s out, node index (irregular rows: a few % of nodes, not counted)
+#   z_merge       s in, 3 out
+#   y_merge       3 in, 2 out
+#   x_merge       2 in + output mask, Ap out, p in (p.Ap fused)
+#   cg_vector     x, r, p, Ap in; x, r out
 def pass_bytes(cls, w, s=4):
-    nx = 2
-    ny = 3
-    return {"x_split": 1 * w + 1 + nx * w, "y_split": (nx + ny) * w, "z_stiff": (ny + 3 * s + 1 + ny) * w,
-            "y_merge": (ny + nx) * w, "x_merge": nx * w + 1 + w}.get(cls)
+    return {"x_split": 5 * w, "y_split": 5 * w, "z_split": (3 + s) * w, "stiff_pointwise": 2 * s * w + 4,
+            "z_merge": (s + 3) * w, "y_merge": 5 * w, "x_merge": 4 * w + 1, "cg_vector": 6 * w}.get(cls)
 
 
 def run_ours(args):

@@ -72,7 +72,8 @@ typedef struct rk_solve_opts {
   double tol;         /* stop when ||F - A d||_2 / ||F||_2 <= tol, FP64 residual (default 1e-10) */
   int32_t max_iter;   /* cap on CG iterations, all refinement steps together (default 200000) */
   int32_t precision;  /* rk_precision (default RK_PREC_MIXED) */
-  double inner_tol;   /* mixed: relative residual target of each FP32 inner solve (default 1e-4) */
+  double inner_tol;   /* mixed: the FP32 CG residual is replaced by the true FP64 residual each time
+                         it has dropped by this factor (default 0.1) */
   int32_t max_outer;  /* mixed: cap on refinement steps (default 60) */
   int32_t check_every;/* iterations between host-side convergence checks (default 25) */
   int32_t x0_given;   /* 1: on entry d holds an initial guess on the free nodes */
@@ -157,8 +158,10 @@ rk_status rk_get_shape(const rk_handle* h, int32_t n[3], int32_t* s, int64_t* n_
  * conjugate gradients solve chi_Omega o K(chi_Omega o x) = F with
  * F = chi_Omega o (f^r - K d_Gamma) until ||F - A x|| <= tol ||F|| (FP64
  * residual); then u^h = Alg. 3 (d).  In RK_PREC_MIXED the CG runs in FP32
- * (FP32 convolutions and vectors, FP64 dot products) inside FP64 iterative
- * refinement (FP64 residual with the FP64 operator).
+ * (FP32 convolutions and vectors, FP64 dot products) and its residual is
+ * periodically replaced by the true FP64 residual (FP64 operator), the FP32
+ * correction being accumulated into the FP64 iterate (iterative refinement
+ * without restarting the Krylov recurrence).
  *   r  [nbox] source (read on chi);  g  [nbox] Dirichlet data (read on chi_gamma)
  *   d  [nbox] output coefficients (input guess if opts->x0_given);  u [nbox] output
  *      u^h (NULL: not computed)
@@ -189,14 +192,15 @@ enum {
   RK_PROF_X_SPLIT = 0,       /* x pass, forward chain (and set-up moments) */
   RK_PROF_Y_SPLIT = 1,       /* y pass, forward chain */
   RK_PROF_Z_SPLIT = 2,       /* z pass of the set-up moments */
-  RK_PROF_Z_STIFF = 3,       /* fused z pass of Alg. 2 */
+  RK_PROF_Z_STIFF = 3,       /* pointwise stage of Alg. 2 (Eq. 90-91) between the z passes */
   RK_PROF_Z_EVAL_U = 4,      /* fused z pass of Alg. 3 */
   RK_PROF_Z_TRANSPOSE_U = 5, /* fused z pass of Alg. 4 / transpose of Alg. 3 */
   RK_PROF_Y_MERGE = 6,       /* y pass, reflected chain */
   RK_PROF_X_MERGE = 7,       /* x pass, reflected chain */
   RK_PROF_MOMENT_SOLVE = 8,  /* per-node M^{-1} of Alg. 1 */
   RK_PROF_CG_VECTOR = 9,     /* CG dot products and vector updates (per iteration) */
-  RK_PROF_CLASSES = 10
+  RK_PROF_Z_MERGE = 10,      /* z pass, reflected chain */
+  RK_PROF_CLASSES = 11
 };
 
 /* Total number of kernels this library has launched in the process. */

@@ -3,7 +3,9 @@
 // sequences the axis passes into the operators of Alg. 1-4 and runs the
 // conjugate-gradient driver of Alg. 5 (plain FP64, or FP32 inner solves inside
 // FP64 iterative refinement).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <array>
@@ -130,6 +132,20 @@ struct rk_handle {
   float* coef32[3] = {nullptr, nullptr, nullptr};
   cpx<double>* tw64[3] = {nullptr, nullptr, nullptr};
   cpx<float>* tw32[3] = {nullptr, nullptr, nullptr};
+  // compressed coefficients of the fused z pass (see ZArgs): node class / index,
+  // table of the irregular nodes, interior values
+  int* cidx = nullptr;
+  double* ctab64 = nullptr;
+  float* ctab32 = nullptr;
+  long long n_irr = 0;
+  double breg64[31] = {};
+  float breg32[31] = {};
+  // TMA descriptors of the z-pass inputs (y-pass outputs) and the device flag a
+  // timed-out tile wait sets
+  bool tma_ok = false;
+  CUtensorMap tm32[6];
+  CUtensorMap tm64[6];
+  int* err_flag = nullptr;
   // workspaces of the operator chains: X outputs, Y outputs, z-pass outputs
   double* ws64 = nullptr;
   float* ws32 = nullptr;
@@ -137,6 +153,8 @@ struct rk_handle {
   double* sv64 = nullptr;  // x, r, p, Ap, F, d0, t0, t1
   float* sv32 = nullptr;   // x, r, p, Ap
   double* partials = nullptr;
+  double* xpartials = nullptr;  // one partial p.Ap per block of the x MERGE pass
+  unsigned* counters2 = nullptr;  // [0]: x MERGE blocks done, [1]: update blocks done
   double* dscal = nullptr;   // scratch scalars (device)
   CGState* cg = nullptr;     // device CG state
   double* hscal = nullptr;   // pinned host scalars
@@ -229,8 +247,9 @@ constexpr int prof_cls(int c) {
   return c + (sizeof(T) == 8 ? RK_PROF_CLASSES : 0);
 }
 
-const char* const kProfNames[RK_PROF_CLASSES] = {"x_split", "y_split", "z_split", "z_stiff", "z_eval_u",
-                                                 "z_transpose_u", "y_merge", "x_merge", "moment_solve", "cg_vector"};
+const char* const kProfNames[RK_PROF_CLASSES] = {"x_split", "y_split", "z_split", "stiff_pointwise", "z_eval_u",
+                                                 "z_transpose_u", "y_merge", "x_merge", "moment_solve", "cg_vector",
+                                                 "z_merge"};
 
 template <typename T>
 const T* coef_of(const rk_handle* h, int axis);
@@ -250,6 +269,19 @@ template <>
 const double* bfields<double>(const rk_handle* h) { return h->b64; }
 template <>
 const float* bfields<float>(const rk_handle* h) { return h->b32; }
+template <typename T>
+const T* ctab_of(const rk_handle* h);
+template <>
+const double* ctab_of<double>(const rk_handle* h) { return h->ctab64; }
+template <>
+const float* ctab_of<float>(const rk_handle* h) { return h->ctab32; }
+template <typename T>
+T breg_of(const rk_handle* h, int j);
+template <>
+double breg_of<double>(const rk_handle* h, int j) { return h->breg64[j]; }
+template <>
+float breg_of<float>(const rk_handle* h, int j) { return h->breg32[j]; }
+
 template <typename T>
 const T* chiV(const rk_handle* h);
 template <>
@@ -284,22 +316,37 @@ rk_status run_split(rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s
 }
 template <typename T>
 rk_status run_merge(rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s) {
-  ProfScope ps(h, prof_cls<T>(axis == 0 ? RK_PROF_X_MERGE : RK_PROF_Y_MERGE), s);
+  ProfScope ps(h, prof_cls<T>(axis == 0 ? RK_PROF_X_MERGE : (axis == 1 ? RK_PROF_Y_MERGE : RK_PROF_Z_MERGE)), s);
   cudaError_t e = launch_merge<T>(axis, h->n[axis], a, s);
   return e == cudaSuccess ? RK_OK : cuda_fail(e, "merge pass");
 }
 
 // Workspace layout of the operator chains: [0, nX) x-pass outputs, [nX, nX+nY)
-// y-pass outputs, [nX+nY, nX+2nY) z-pass outputs.
-inline int ws_fields(const Chain& c) { return c.nX + 2 * c.nY; }
+// y-pass outputs, [nX+nY, nX+2nY) z-pass outputs, [nX+2nY, nX+2nY+s) the fields
+// D_p / g_p of the z axis of Alg. 2.
+inline int ws_fields(const Chain& c) { return c.nX + 2 * c.nY + c.s; }
+
+// CG step fused into the x passes of A p: p = r + beta p before the x SPLIT uses
+// it, p . Ap (and alpha) after the x MERGE writes Ap.
+template <typename T>
+struct CGFuse {
+  T* p;
+  const T* r;
+};
 
 // forward chain, x and y passes: E_{mx,my} = conv_x conv_y (mask o d)   (Alg. 2 line 1-2)
 template <typename T>
-rk_status chain_forward_xy(rk_handle* h, const T* d, const uint8_t* in_mask, cudaStream_t s) {
+rk_status chain_forward_xy(rk_handle* h, const T* d, const uint8_t* in_mask, cudaStream_t s,
+                           const CGFuse<T>* fuse = nullptr) {
   const Chain& c = h->chain;
   PassArgs<T> ax = pass_base<T>(h, 0);
   ax.in[0] = d;
   ax.in_mask = in_mask;
+  if (fuse) {
+    ax.cg_p = fuse->p;
+    ax.cg_r = fuse->r;
+    ax.cg = h->cg;
+  }
   ax.n_groups = 1;
   ax.g_io[0] = 0;
   ax.g_begin[0] = 0;
@@ -331,7 +378,8 @@ rk_status chain_forward_xy(rk_handle* h, const T* d, const uint8_t* in_mask, cud
 
 // reflected chain, y and x passes: f = out_mask o sum conv_x(Hbar) conv_y(Hbar) G   (Alg. 2 last line)
 template <typename T>
-rk_status chain_reflect_yx(rk_handle* h, T* f, const uint8_t* out_mask, cudaStream_t s) {
+rk_status chain_reflect_yx(rk_handle* h, T* f, const uint8_t* out_mask, cudaStream_t s,
+                           const CGFuse<T>* fuse = nullptr) {
   const Chain& c = h->chain;
   PassArgs<T> ay = pass_base<T>(h, 1);
   ay.reflect = 1;
@@ -354,6 +402,12 @@ rk_status chain_reflect_yx(rk_handle* h, T* f, const uint8_t* out_mask, cudaStre
   PassArgs<T> ax = pass_base<T>(h, 0);
   ax.reflect = 1;
   ax.out_mask = out_mask;
+  if (fuse) {
+    ax.cg_p = fuse->p;
+    ax.cg = h->cg;
+    ax.partials = h->xpartials;
+    ax.counter = h->counters2;
+  }
   ax.n_groups = 1;
   ax.out[0] = f;
   ax.g_io[0] = 0;
@@ -401,18 +455,63 @@ rk_status run_z(rk_handle* h, int mode, const ZArgs<T>& a, cudaStream_t s) {
   return e == cudaSuccess ? RK_OK : cuda_fail(e, "z pass");
 }
 
-// Alg. 2: f = out_mask o K (in_mask o d)
+// Alg. 2: f = out_mask o K (in_mask o d).  The z axis runs as three kernels: a
+// SPLIT along z (E_(ax,ay) -> D_p, p = 1..s), the pointwise stage of Eq. 90-91 in
+// place (D_p -> g_p), and a reflected MERGE along z (g_p -> G_(ax,ay)).
 template <typename T>
-rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uint8_t* out_mask, cudaStream_t s) {
-  RK_TRY(chain_forward_xy<T>(h, d, in_mask, s));
-  ZArgs<T> z = z_base<T>(h);
-  for (int g = 0; g < h->chain.nY; ++g) {
-    z.in[g] = h->ws<T>(h->chain.nX + g);
-    z.out[g] = h->ws<T>(h->chain.nX + h->chain.nY + g);
+rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uint8_t* out_mask, cudaStream_t s,
+               const CGFuse<T>* fuse = nullptr) {
+  const Chain& c = h->chain;
+  RK_TRY(chain_forward_xy<T>(h, d, in_mask, s, fuse));
+  const int dbase = c.nX + 2 * c.nY;  // D_p / g_p fields
+  PassArgs<T> az = pass_base<T>(h, 2);
+  az.n_groups = c.nY;
+  int q = 0;
+  for (int g = 0; g < c.nY; ++g) {
+    az.in[g] = h->ws<T>(c.nX + g);
+    az.g_io[g] = g;
+    az.g_begin[g] = q;
+    for (auto& t : c.zterms[g]) {
+      az.out[t.second] = h->ws<T>(dbase + t.second);
+      az.term_io[q] = t.second;
+      az.term_m[q] = t.first;
+      ++q;
+    }
   }
-  z.wfield = chiV<T>(h);
-  RK_TRY(run_z<T>(h, Z_STIFF, z, s));
-  return chain_reflect_yx<T>(h, f, out_mask, s);
+  az.g_begin[c.nY] = q;
+  RK_TRY(run_split<T>(h, 2, az, s));
+  PointwiseArgs<T> pw;
+  memset(&pw, 0, sizeof(pw));
+  for (int p = 0; p < h->s; ++p) pw.D[p] = h->ws<T>(dbase + p);
+  pw.s = h->s;
+  pw.cidx = h->cidx;
+  pw.ctab = ctab_of<T>(h);
+  pw.n_irr = h->n_irr;
+  for (int j = 0; j < 3 * h->s + 1; ++j) pw.breg[j] = breg_of<T>(h, j);
+  pw.nbox = h->nbox;
+  {
+    ProfScope ps(h, prof_cls<T>(RK_PROF_Z_STIFF), s);
+    cudaError_t e = launch_pointwise_stiff<T>(pw, s);
+    if (e != cudaSuccess) return cuda_fail(e, "pointwise stage");
+  }
+  PassArgs<T> rz = pass_base<T>(h, 2);
+  rz.reflect = 1;
+  rz.n_groups = c.nY;
+  q = 0;
+  for (int g = 0; g < c.nY; ++g) {
+    rz.out[g] = h->ws<T>(c.nX + c.nY + g);
+    rz.g_io[g] = g;
+    rz.g_begin[g] = q;
+    for (auto& t : c.zterms[g]) {
+      rz.in[t.second] = h->ws<T>(dbase + t.second);
+      rz.term_io[q] = t.second;
+      rz.term_m[q] = t.first;
+      ++q;
+    }
+  }
+  rz.g_begin[c.nY] = q;
+  RK_TRY(run_merge<T>(h, 2, rz, s));
+  return chain_reflect_yx<T>(h, f, out_mask, s, fuse);
 }
 
 // Alg. 3: u = chi o sum_p b^0_p o conv(chi o d, H^a_p)
@@ -560,6 +659,11 @@ rk_status ensure_solver(rk_handle* h) {
   if (!h->sv64) RK_TRY(h->alloc(&h->sv64, (size_t)8 * h->nbox));
   if (!h->sv32) RK_TRY(h->alloc(&h->sv32, (size_t)4 * h->nbox));
   if (!h->partials) RK_TRY(h->alloc(&h->partials, (size_t)kRedBlocks));
+  if (!h->xpartials) RK_TRY(h->alloc(&h->xpartials, (size_t)((long long)h->n[1] * h->n[2] / 2 + 1)));
+  if (!h->counters2) {
+    RK_TRY(h->alloc(&h->counters2, (size_t)2));
+    RK_CK(cudaMemset(h->counters2, 0, 2 * sizeof(unsigned)));
+  }
   if (!h->dscal) RK_TRY(h->alloc(&h->dscal, (size_t)8));
   if (!h->cg) RK_TRY(h->alloc(&h->cg, (size_t)1));
   if (!h->hscal) {
@@ -610,15 +714,15 @@ rk_status cg_run(rk_handle* h, T* x, T* r, T* p, T* Ap, double rr_target, int ma
       }
       if (!(rr > rr_target) || it >= max_iter) break;
     }
-    RK_TRY(op_K<T>(h, p, Ap, h->chi_omega, h->chi_omega, s));
+    // one iteration: p = r + beta p (x pass prologue), Ap (p is zero off chi_Omega,
+    // so only the output mask applies), p.Ap -> alpha (x pass epilogue), then
+    // x += alpha p, r -= alpha Ap, r.r -> beta
+    const CGFuse<T> fz{p, r};
+    RK_TRY(op_K<T>(h, p, Ap, nullptr, h->chi_omega, s, &fz));
     ++*matvecs;
     {
       ProfScope ps(h, prof_cls<T>(RK_PROF_CG_VECTOR), s);
-      RK_CK(launch_dot<T, T>(p, Ap, n, h->partials, h->dscal, s));
-      RK_CK(launch_cg_alpha(h->partials, h->cg, s));
-      RK_CK(launch_cg_xr<T>(x, r, p, Ap, h->cg, n, h->partials, s));
-      RK_CK(launch_cg_beta(h->partials, h->cg, s));
-      RK_CK(launch_cg_p<T>(p, r, h->cg, n, s));
+      RK_CK(launch_cg_xr_fused<T>(x, r, p, Ap, h->cg, n, h->partials, h->counters2 + 1, s));
     }
     ++it;
   }
@@ -668,34 +772,65 @@ rk_status solve_masked(rk_handle* h, const double* F, double* x, const rk_solve_
       RK_TRY(true_residual(&rn));
     }
   } else {
+    // One FP32 CG (FP32 K.u and vectors, FP64 dot products) whose recurrence
+    // residual is replaced by the true FP64 residual F - A64 x64 whenever it has
+    // dropped by the factor inner_tol since the last replacement; the FP32 update
+    // accumulated since then is added to the FP64 iterate first.  The search
+    // direction is kept across replacements, so the Krylov space is not lost.
     float* x32 = h->v32(0);
     float* r32 = h->v32(1);
     float* p32 = h->v32(2);
     float* Ap32 = h->v32(3);
-    double prev = rn;
+    RK_CK(launch_to_f32(r32, r64, 1.0, n, s));
+    RK_CK(launch_fill<float>(x32, 0.0f, n, s));
+    RK_CK(launch_copy<float>(p32, r32, n, s));
+    RK_CK(launch_dot<float, float>(r32, r32, n, h->partials, h->dscal, s));
+    RK_CK(launch_cg_init(h->partials, h->cg, s));
+    double rmax = rn;
+    double best = rn;
     int stall = 0;
-    while (rn > target && info->outer < o.max_outer && total < o.max_iter) {
-      // inner FP32 solve of A c = r / |r|, to relative residual inner_tol
-      RK_CK(launch_to_f32(r32, r64, 1.0 / rn, n, s));
-      RK_CK(launch_fill<float>(x32, 0.0f, n, s));
-      const double it_tol = std::max(o.inner_tol, 0.5 * target / rn);
-      int it = 0, mv = 0;
-      double rr;
-      rk_status st = cg_run<float>(h, x32, r32, p32, Ap32, it_tol * it_tol, o.max_iter - total, o.check_every, s,
-                                  &it, &rr, &mv);
-      total += it;
-      info->matvec_f32 += mv;
-      info->outer++;
-      if (st != RK_OK && st != RK_ERR_BREAKDOWN) return st;
-      RK_CK(launch_acc_f32(x, x32, rn, n, s));
-      RK_TRY(true_residual(&rn));
-      if (rn > 0.9 * prev) {
-        if (++stall >= 3) break;
-      } else {
-        stall = 0;
+    int it = 0;
+    for (;;) {
+      if (it % o.check_every == 0 || it >= o.max_iter) {
+        RK_CK(cudaMemcpyAsync(h->hscal, h->cg, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+        RK_CK(cudaStreamSynchronize(s));
+        CGState cs;
+        memcpy(&cs, h->hscal, sizeof(CGState));
+        const double rest = std::sqrt(std::max(cs.rr, 0.0));
+        if (cs.flag || rest <= o.inner_tol * rmax || rest <= 0.5 * target || it >= o.max_iter) {
+          // residual replacement: x64 += x32, r64 = F - A64 x64, r32 = r64
+          RK_CK(launch_acc_f32(x, x32, 1.0, n, s));
+          RK_CK(launch_fill<float>(x32, 0.0f, n, s));
+          RK_TRY(true_residual(&rn));
+          info->outer++;
+          if (rn <= target || it >= o.max_iter) break;
+          if (rn < best) {
+            best = rn;
+            stall = 0;
+          } else if (++stall >= 4) {
+            break;  // FP32 recurrence no longer reduces the FP64 residual
+          }
+          RK_CK(launch_to_f32(r32, r64, 1.0, n, s));
+          RK_CK(launch_dot<float, float>(r32, r32, n, h->partials, h->dscal, s));
+          if (cs.flag) {  // restart the direction after a breakdown
+            RK_CK(launch_copy<float>(p32, r32, n, s));
+            RK_CK(launch_cg_init(h->partials, h->cg, s));
+          } else {
+            RK_CK(launch_cg_set_rr(h->partials, h->cg, s));
+          }
+          rmax = rn;
+        }
       }
-      prev = rn;
+      const CGFuse<float> fz{p32, r32};
+      RK_TRY(op_K<float>(h, p32, Ap32, nullptr, h->chi_omega, s, &fz));
+      info->matvec_f32++;
+      {
+        ProfScope ps(h, prof_cls<float>(RK_PROF_CG_VECTOR), s);
+        RK_CK(launch_cg_xr_fused<float>(x32, r32, p32, Ap32, h->cg, n, h->partials, h->counters2 + 1, s));
+      }
+      ++it;
     }
+    total = it;
   }
   info->iterations = total;
   info->rel_residual = rn / fn;
@@ -707,7 +842,7 @@ void fill_defaults(rk_solve_opts* o) {
   o->tol = 1e-10;
   o->max_iter = 200000;
   o->precision = RK_PREC_MIXED;
-  o->inner_tol = 1e-4;
+  o->inner_tol = 0.1;
   o->max_outer = 60;
   o->check_every = 25;
   o->x0_given = 0;
@@ -747,6 +882,122 @@ rk_status forward_solve(rk_handle* h, const double* r, const double* g, double* 
   rk_status st = solve_masked(h, F, x, o, info, s);
   RK_CK(launch_add(d, d0, x, n, s));
   return st;
+}
+
+// Tensor maps of the y-pass outputs (inputs of the fused z pass): 3D x-fastest
+// fields, box {2L, 1, n_z} = one pencil of 2L adjacent x.  Left disabled (the
+// non-TMA kernel runs) when the driver entry point or the encoding is unavailable.
+template <typename T>
+bool encode_z_maps(rk_handle* h, CUtensorMap* maps, PFN_cuTensorMapEncodeTiled_v12000 enc) {
+  for (int g = 0; g < h->chain.nY; ++g) {
+    void* addr = h->ws<T>(h->chain.nX + g);
+    cuuint64_t dims[3] = {(cuuint64_t)h->n[0], (cuuint64_t)h->n[1], (cuuint64_t)h->n[2]};
+    cuuint64_t strides[2] = {(cuuint64_t)h->n[0] * sizeof(T), (cuuint64_t)h->n[0] * h->n[1] * sizeof(T)};
+    cuuint32_t box[3] = {(cuuint32_t)(2 * z_pairs<T>()), 1u, (cuuint32_t)h->n[2]};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (box[2] > 256 || (strides[0] % 16) || (strides[1] % 16)) return false;
+    CUresult r = enc(&maps[g], sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                     addr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+  }
+  return true;
+}
+
+rk_status setup_tma(rk_handle* h) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    h->tma_ok = false;
+    return RK_OK;
+  }
+  auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  RK_TRY(h->alloc(&h->err_flag, 1));
+  RK_CK(cudaMemset(h->err_flag, 0, sizeof(int)));
+  h->tma_ok = encode_z_maps<float>(h, h->tm32, enc) && encode_z_maps<double>(h, h->tm64, enc);
+  return RK_OK;
+}
+
+// RK_ERR_TIMEOUT if a bounded device wait gave up since the last check (flag cleared).
+rk_status check_device_flag(rk_handle* h) {
+  if (!h->err_flag) return RK_OK;
+  int f = 0;
+  RK_CK(cudaMemcpy(&f, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost));
+  if (f) {
+    RK_CK(cudaMemset(h->err_flag, 0, sizeof(int)));
+    return fail(RK_ERR_TIMEOUT, "a TMA tile wait of the z pass timed out");
+  }
+  return RK_OK;
+}
+
+// A node is regular when its whole support (+-reach on every axis) lies in chi and
+// its V equals the V of the first such node: its moment matrix (Eq. 48) and hence
+// b and chi V are then those of every other regular node.  Regular nodes are
+// served from 3s+1 interior values, irregular ones from a compact table in node
+// order.
+rk_status compress_coefficients(rk_handle* h, cudaStream_t s) {
+  const long long n = h->nbox;
+  const int nblk = (int)((n + kScanBlock - 1) / kScanBlock);
+  uint8_t* tmp = nullptr;
+  int* counts = nullptr;
+  cudaError_t e = cudaMalloc((void**)&tmp, (size_t)3 * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&counts, sizeof(int) * ((size_t)nblk + 1));
+  auto done = [&](rk_status st) {
+    cudaFree(tmp);
+    cudaFree(counts);
+    return st;
+  };
+  if (e != cudaSuccess) return done(cuda_fail(e, "compression workspace"));
+  uint8_t *ea = tmp, *eb = tmp + n, *cls = tmp + 2 * n;
+  if ((e = launch_erode(ea, h->chi, 0, h->reach, h->n, s)) != cudaSuccess ||
+      (e = launch_erode(eb, ea, 1, h->reach, h->n, s)) != cudaSuccess ||
+      (e = launch_erode(ea, eb, 2, h->reach, h->n, s)) != cudaSuccess)
+    return done(cuda_fail(e, "erode"));
+  std::vector<uint8_t> er((size_t)n);
+  if ((e = cudaMemcpyAsync(er.data(), ea, (size_t)n, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return done(cuda_fail(e, "copy eroded mask"));
+  long long reg = -1;
+  for (long long i = 0; i < n; ++i)
+    if (er[(size_t)i]) {
+      reg = i;
+      break;
+    }
+  double vreg = std::nan("");
+  if (reg >= 0 && (e = cudaMemcpy(&vreg, h->V + reg, sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return done(cuda_fail(e, "read V"));
+  int total = 0;
+  if ((e = launch_classify(cls, h->chi, ea, h->V, vreg, n, s)) != cudaSuccess ||
+      (e = launch_count_irregular(cls, n, counts, s)) != cudaSuccess ||
+      (e = launch_scan_counts(counts, nblk, counts + nblk, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&total, counts + nblk, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return done(cuda_fail(e, "classify"));
+  h->n_irr = total;
+  const int ncoef = 3 * h->s + 1;
+  rk_status st;
+  if ((st = h->alloc(&h->cidx, (size_t)n)) != RK_OK || (st = h->alloc(&h->ctab64, (size_t)ncoef * total)) != RK_OK ||
+      (st = h->alloc(&h->ctab32, (size_t)ncoef * total)) != RK_OK)
+    return done(st);
+  if ((e = launch_compact<double>(cls, counts, n, h->cidx, h->b64, h->s, h->chiV64, h->ctab64, total, s)) !=
+          cudaSuccess ||
+      (e = launch_compact<float>(cls, counts, n, h->cidx, h->b32, h->s, h->chiV32, h->ctab32, total, s)) !=
+          cudaSuccess)
+    return done(cuda_fail(e, "compact"));
+  if (reg >= 0) {
+    double* g = nullptr;
+    if ((e = cudaMalloc((void**)&g, sizeof(double) * (size_t)ncoef)) != cudaSuccess) return done(cuda_fail(e, "gather"));
+    e = launch_gather(g, h->b64 + (size_t)h->s * n, n, reg, 3 * h->s, s);
+    if (e == cudaSuccess) e = launch_gather(g + 3 * h->s, h->chiV64, 0, reg, 1, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->breg64, g, sizeof(double) * ncoef, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(g);
+    if (e != cudaSuccess) return done(cuda_fail(e, "gather"));
+    for (int j = 0; j < ncoef; ++j) h->breg32[j] = (float)h->breg64[j];
+  }
+  return done(RK_OK);
 }
 
 }  // namespace
@@ -1003,6 +1254,8 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
   st = run_setup();
   cudaFree(mws);
   if (st != RK_OK) return bail(st);
+  if ((st = compress_coefficients(h, s)) != RK_OK) return bail(st);
+  if ((st = setup_tma(h)) != RK_OK) return bail(st);
   *out = h;
   if (h->n_singular)
     return fail(RK_ERR_SINGULAR_MOMENT,
@@ -1120,6 +1373,7 @@ rk_status rk_solve(rk_handle* h, const double* r, const double* g, double* d, do
     RK_TRY(stage_out_finish(su, s));
   }
   RK_CK(cudaStreamSynchronize(s));
+  if (st == RK_OK) st = check_device_flag(h);
   inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   inf.status = st;
   if (info) *info = inf;

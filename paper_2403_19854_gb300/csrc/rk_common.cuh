@@ -68,6 +68,40 @@ template <typename T>
 RK_HD cpx<T> cmulc(cpx<T> a, cpx<T> b) { return cmk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }
 template <typename T>
 RK_HD cpx<T> cscale(cpx<T> a, T s) { return cmk(a.x * s, a.y * s); }
+// element-wise products of the two components (two real lines / node pairs)
+template <typename T>
+RK_HD cpx<T> pmul(cpx<T> a, cpx<T> b) { return cmk(a.x * b.x, a.y * b.y); }
+template <typename T>
+RK_HD cpx<T> pfma(cpx<T> a, cpx<T> b, cpx<T> c) { return cmk(a.x * b.x + c.x, a.y * b.y + c.y); }
+
+// FP32 pairs use the packed two-lane FP32 instructions of sm_100+ (one
+// instruction per component pair); other targets keep the scalar forms above.
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+#define RK_PACKED_F32 1
+__device__ __forceinline__ float2 rk_f2(cpx<float> a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ cpx<float> rk_c2(float2 a) { return cmk(a.x, a.y); }
+__device__ __forceinline__ cpx<float> operator+(cpx<float> a, cpx<float> b) {
+  return rk_c2(__fadd2_rn(rk_f2(a), rk_f2(b)));
+}
+__device__ __forceinline__ cpx<float> operator-(cpx<float> a, cpx<float> b) {
+  return rk_c2(__fadd2_rn(rk_f2(a), make_float2(-b.x, -b.y)));
+}
+__device__ __forceinline__ cpx<float> cmul(cpx<float> a, cpx<float> b) {
+  // (a.x b.x - a.y b.y, a.x b.y + a.y b.x) = a.x (b.x, b.y) + a.y (-b.y, b.x)
+  return rk_c2(__ffma2_rn(make_float2(a.y, a.y), make_float2(-b.y, b.x), __fmul2_rn(make_float2(a.x, a.x), rk_f2(b))));
+}
+__device__ __forceinline__ cpx<float> cmulc(cpx<float> a, cpx<float> b) {
+  // a conj(b) = (a.x b.x + a.y b.y, a.y b.x - a.x b.y) = b.x (a.x, a.y) + b.y (a.y, -a.x)
+  return rk_c2(__ffma2_rn(make_float2(b.y, b.y), make_float2(a.y, -a.x), __fmul2_rn(make_float2(b.x, b.x), rk_f2(a))));
+}
+__device__ __forceinline__ cpx<float> cscale(cpx<float> a, float s) {
+  return rk_c2(__fmul2_rn(rk_f2(a), make_float2(s, s)));
+}
+__device__ __forceinline__ cpx<float> pmul(cpx<float> a, cpx<float> b) { return rk_c2(__fmul2_rn(rk_f2(a), rk_f2(b))); }
+__device__ __forceinline__ cpx<float> pfma(cpx<float> a, cpx<float> b, cpx<float> c) {
+  return rk_c2(__ffma2_rn(rk_f2(a), rk_f2(b), rk_f2(c)));
+}
+#endif
 // multiply by i*s (s real)
 template <typename T>
 RK_HD cpx<T> ciscale(cpx<T> a, T s) { return cmk(-a.y * s, a.x * s); }
@@ -152,8 +186,7 @@ RK_HD cpx<T> twmul(cpx<T> v) {
   } else if constexpr (W::minus_i) {
     return cmk(v.y, -v.x);
   } else {
-    const T c = (T)W::c, s = (T)W::s;
-    return cmk(v.x * c - v.y * s, v.x * s + v.y * c);
+    return cmul(v, cmk((T)W::c, (T)W::s));
   }
 }
 
@@ -227,8 +260,8 @@ struct DFTOddPrime {
         constexpr int j = decltype(J)::value + 1;
         constexpr double c = trig::cos2pi(j * k, R);
         constexpr double s = DIR * trig::sin2pi(j * k, R);
-        re = re + cscale(t[j - 1], (T)c);
-        im = im + cscale(u[j - 1], (T)s);
+        re = pfma(t[j - 1], cmk((T)c, (T)c), re);
+        im = pfma(u[j - 1], cmk((T)s, (T)s), im);
       });
       // + i*im and - i*im
       out[k] = cmk(re.x - im.y, re.y + im.x);

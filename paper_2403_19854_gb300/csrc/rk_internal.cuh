@@ -14,6 +14,12 @@ namespace rk {
 extern std::atomic<long long> g_launches;
 inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+// Node pairs per block of the fused z pass (tile width 2L values, 64 bytes).
+template <typename T>
+constexpr int z_pairs() {
+  return sizeof(T) == 4 ? 8 : 4;
+}
+
 // Line lengths with instantiated FFT kernels.
 bool supported_length(int n);
 
@@ -45,16 +51,43 @@ struct MomentArgs {
 };
 cudaError_t launch_moment_solve(const MomentArgs& a, cudaStream_t s);
 
-// ------------------------------------------------------------ CG kernels
-struct CGState {
-  double rr;      // r.r of the current iterate
-  double pAp;
-  double alpha;
-  double beta;
-  double rr_new;
-  int flag;       // 1: breakdown (p^T A p <= 0 or not finite)
-  int pad;
+// ------------------------------------------------- coefficient compression
+// out = 1 where every node within +-r along `axis` (periodic) has in = 1.
+cudaError_t launch_erode(uint8_t* out, const uint8_t* in, int axis, int r, const int n[3], cudaStream_t s);
+// cls = 0 (chi = 0), 1 (regular: eroded and V == vreg), 2 (irregular)
+cudaError_t launch_classify(uint8_t* cls, const uint8_t* chi, const uint8_t* eroded, const double* V, double vreg,
+                            long long n, cudaStream_t s);
+constexpr int kScanBlock = 1024;  // nodes per compaction block
+// per-block counts of class 2 -> counts[nblk]
+cudaError_t launch_count_irregular(const uint8_t* cls, long long n, int* counts, cudaStream_t s);
+// exclusive scan of counts (single block, in place); total -> *total
+cudaError_t launch_scan_counts(int* counts, int nblk, int* total, cudaStream_t s);
+// cidx = -1 / 0 / 1 + compact index; table rows [ncoef][n_irr] filled from b (families 1..3) and chiV
+template <typename T>
+cudaError_t launch_compact(const uint8_t* cls, const int* offsets, long long n, int* cidx, const T* b, int s,
+                           const T* chiV, T* tab, long long n_irr, cudaStream_t st);
+// out[j] = src[j * stride + idx] for j < count
+cudaError_t launch_gather(double* out, const double* src, long long stride, long long idx, int count, cudaStream_t s);
+
+// --------------------------------------------- pointwise stage of Alg. 2
+// In place over the s fields D_p (z-pass outputs of the forward chain):
+//   A^k = sum_q b^k_q D_q (Eq. 90),  g_p = chi V sum_k b^k_p A^k (Eq. 91),
+// with the coefficients of a node from breg (cidx = 0), from row cidx - 1 of ctab
+// (cidx > 0), or g = 0 off chi (cidx = -1).
+template <typename T>
+struct PointwiseArgs {
+  T* D[10];
+  int s;
+  const int* cidx;
+  const T* ctab;
+  long long n_irr;
+  T breg[31];
+  long long nbox;
 };
+template <typename T>
+cudaError_t launch_pointwise_stiff(const PointwiseArgs<T>& a, cudaStream_t s);
+
+// ------------------------------------------------------------ CG kernels
 
 constexpr int kRedBlocks = 608;  // 4 x 152 SMs; fixed so reductions are deterministic
 constexpr int kRedThreads = 256;
@@ -69,6 +102,12 @@ cudaError_t launch_cg_beta(const double* partials, CGState* st, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cg_p(T* p, const T* r, const CGState* st, long long n, cudaStream_t s);
 cudaError_t launch_cg_init(const double* partials, CGState* st, cudaStream_t s);
+// rr = sum(partials), leaving beta and the search direction as they are
+cudaError_t launch_cg_set_rr(const double* partials, CGState* st, cudaStream_t s);
+// x += alpha p, r -= alpha Ap; the last block sets rr_new, beta = rr_new / rr, rr = rr_new
+template <typename T>
+cudaError_t launch_cg_xr_fused(T* x, T* r, const T* p, const T* Ap, CGState* st, long long n, double* partials,
+                               unsigned* counter, cudaStream_t s);
 
 // elementwise helpers (double unless noted)
 cudaError_t launch_dirichlet_d0(double* d0, const double* g, const uint8_t* chi_gamma, long long n, cudaStream_t s);

@@ -2,7 +2,10 @@
 // per-precision translation units, which instantiate it for float and double.
 #pragma once
 
+#include <algorithm>
+
 #include "rk_internal.cuh"
+#include "rk_zpass_tma.cuh"
 
 namespace rk {
 
@@ -13,14 +16,14 @@ struct Cfg;
 template <>
 struct Cfg<float> {
   static constexpr int L = 16;
-  static constexpr int XTHREADS = 256;
-  static constexpr int LZ = 8;
+  static constexpr int XTHREADS = 128;
+  static constexpr int LZ = z_pairs<float>();
 };
 template <>
 struct Cfg<double> {
   static constexpr int L = 8;
   static constexpr int XTHREADS = 128;
-  static constexpr int LZ = 4;
+  static constexpr int LZ = z_pairs<double>();
 };
 
 template <typename K>
@@ -79,8 +82,34 @@ cudaError_t merge_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+inline int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+  }
+  return n;
+}
+
+// persistent TMA-pipelined Z_STIFF: two resident blocks per SM
+template <typename T, int N>
+cudaError_t z_stiff_tma(const ZArgs<T>& a, cudaStream_t s) {
+  constexpr int L = Cfg<T>::LZ;
+  using Z = ZTma<T, N, L>;
+  const long long npen = (long long)((a.nx / 2 + L - 1) / L) * a.ny;
+  const long long nb = std::min<long long>(npen, 2LL * sm_count());
+  auto k = k_z_stiff_tma<T, N, L>;
+  cudaError_t e = set_smem(k, Z::SMEM);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  k<<<(unsigned)nb, Z::THREADS, Z::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, int N, int MODE>
 cudaError_t z_n_mode(const ZArgs<T>& a, cudaStream_t s) {
+  if (MODE == Z_STIFF && a.use_tma && a.cidx) return z_stiff_tma<T, N>(a, s);
   constexpr int L = Cfg<T>::LZ;
   using Z = ZPass<T, N, L, MODE>;
   dim3 grid((unsigned)((a.nx / 2 + L - 1) / L), (unsigned)a.ny);

@@ -22,6 +22,8 @@
 //   y and z lines: pairs of adjacent x (a float2/double2 per node pair).
 #pragma once
 
+#include <cuda.h>
+
 #include "rk_linefft.cuh"
 
 namespace rk {
@@ -38,6 +40,17 @@ RK_HD cpx<T> spec_mul(cpx<T> v, const T* __restrict__ coef, int N, int m, int k,
   if (reflect && (m & 1)) c = -c;
   return (m & 1) ? ciscale(v, c) : cscale(v, c);
 }
+
+// Scalars of the conjugate-gradient recurrence, kept in device memory.
+struct CGState {
+  double rr;      // r.r of the current iterate
+  double pAp;
+  double alpha;
+  double beta;
+  double rr_new;
+  int flag;       // 1: breakdown (p^T A p <= 0 or not finite)
+  int pad;
+};
 
 template <typename T>
 struct PassArgs {
@@ -56,6 +69,13 @@ struct PassArgs {
   int nx, ny, nz;
   long long line_stride;      // strided passes: element stride along the line
   long long other_stride;     // strided passes: stride of blockIdx.y
+  // CG iteration fused into the x passes of A p (x SPLIT prologue, x MERGE epilogue):
+  T* cg_p;                    // SPLIT: p, updated in place to r + beta p before use
+                              // MERGE: p, for the product p . (A p) of the output
+  const T* cg_r;              // SPLIT: r (prologue active when non-null)
+  CGState* cg;                // beta (read); pAp, alpha, flag (written by the last MERGE block)
+  double* partials;           // MERGE: one partial p.Ap per block
+  unsigned* counter;          // MERGE: blocks finished (the last one reduces and resets it)
 };
 
 // ---------------------------------------------------------------- strided passes
@@ -163,6 +183,52 @@ RK_DEV T mask_of(const uint8_t* m, long long i) {
   return m ? (T)RK_LDG(m + i) : (T)1;
 }
 
+// p . Ap of the x MERGE epilogue: block sum in a fixed tree order, one partial
+// per block; the last block to finish sums the partials in block order (so the
+// result is reproducible), sets pAp and alpha = rr / pAp (flag on breakdown) and
+// resets the counter.
+template <int THREADS, typename T>
+__device__ __forceinline__ void cg_pap_reduce(double v, const PassArgs<T>& a) {
+  __shared__ double red[THREADS];
+  __shared__ bool last;
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = THREADS / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.partials[blockIdx.x] = red[0];
+    __threadfence();
+    last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += THREADS) s += ((volatile double*)a.partials)[b];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = THREADS / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double pap = red[0];
+    CGState* st = a.cg;
+    st->pAp = pap;
+    double al = 0.0;
+    if (st->rr > 0.0) {
+      if (pap > 0.0 && isfinite(pap))
+        al = st->rr / pap;
+      else
+        st->flag = 1;
+    }
+    st->alpha = al;
+    *a.counter = 0u;
+  }
+}
+
 template <typename T, int N, int LX>
 __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_split(const PassArgs<T> a) {
   using X = XPass<T, N, LX>;
@@ -177,12 +243,29 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_split(const Pass
   cpx<T> v[X::R], w[X::R];
   for (int g = 0; g < a.n_groups; ++g) {
     const T* in = a.in[a.g_io[g]];
+    if (a.cg_r) {
+      // CG direction update fused into the load: p = r + beta p (Alg. 5, CG step)
+      const T be = (T)a.cg->beta;
 #pragma unroll
-    for (int r = 0; r < X::R; ++r) {
-      const int xp = F::nat_pos(t, r);
-      v[r] = ok ? cmk(RK_LDG(in + r0 + xp) * mask_of<T>(a.in_mask, r0 + xp),
-                      RK_LDG(in + r1 + xp) * mask_of<T>(a.in_mask, r1 + xp))
-                : cmk((T)0, (T)0);
+      for (int r = 0; r < X::R; ++r) {
+        const int xp = F::nat_pos(t, r);
+        T p0 = (T)0, p1 = (T)0;
+        if (ok) {
+          p0 = a.cg_r[r0 + xp] + be * a.cg_p[r0 + xp];
+          p1 = a.cg_r[r1 + xp] + be * a.cg_p[r1 + xp];
+          a.cg_p[r0 + xp] = p0;
+          a.cg_p[r1 + xp] = p1;
+        }
+        v[r] = cmk(p0, p1);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) {
+        const int xp = F::nat_pos(t, r);
+        v[r] = ok ? cmk(RK_LDG(in + r0 + xp) * mask_of<T>(a.in_mask, r0 + xp),
+                        RK_LDG(in + r1 + xp) * mask_of<T>(a.in_mask, r1 + xp))
+                  : cmk((T)0, (T)0);
+      }
     }
     F::forward(v, t, buf, a.tw);
     for (int qq = a.g_begin[g]; qq < a.g_begin[g + 1]; ++qq) {
@@ -231,13 +314,18 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_merge(const Pass
     }
     F::inverse(acc, t, buf, a.tw);
     T* out = a.out[a.g_io[g]];
+    double dot = 0.0;
     if (ok)
 #pragma unroll
       for (int r = 0; r < X::R; ++r) {
         const int xp = F::nat_pos(t, r);
-        out[r0 + xp] = acc[r].x * mask_of<T>(a.out_mask, r0 + xp);
-        out[r1 + xp] = acc[r].y * mask_of<T>(a.out_mask, r1 + xp);
+        const T o0 = acc[r].x * mask_of<T>(a.out_mask, r0 + xp);
+        const T o1 = acc[r].y * mask_of<T>(a.out_mask, r1 + xp);
+        out[r0 + xp] = o0;
+        out[r1 + xp] = o1;
+        if (a.cg_p) dot += (double)a.cg_p[r0 + xp] * (double)o0 + (double)a.cg_p[r1 + xp] * (double)o1;
       }
+    if (a.cg_p) cg_pap_reduce<X::THREADS>(dot, a);
   }
 }
 
@@ -263,6 +351,21 @@ struct ZArgs {
   const cpx<T>* tw;      // z-axis twiddles
   int nx, ny, nz;
   long long nbox;
+  // Z_STIFF with compressed coefficients (cidx != nullptr): per node -1 (outside
+  // chi), 0 (regular: the support lies in chi and V is the interior V, so b equals
+  // the interior values breg), or 1 + row of ctab.  ctab is [3s+1][n_irr]:
+  // b^x_p, b^y_p, b^z_p (s each) and chi V of the irregular nodes; breg the same
+  // 3s+1 values of a regular node.  With cidx == nullptr the full fields b and
+  // wfield are read instead.
+  const int* cidx;
+  const T* ctab;
+  long long n_irr;
+  T breg[3 * 10 + 1];
+  // Z_STIFF input tiles by TMA (use_tma = 1): one tensor map per input field,
+  // box {2L, 1, N} of the x-fastest field; err receives 1 if a tile wait ran out.
+  int use_tma;
+  int* err;
+  CUtensorMap tmap[6];
 };
 
 template <typename T, int N, int L, int MODE>
@@ -272,7 +375,7 @@ struct ZPass {
   static constexpr int P = F::P, R = F::R;
   static constexpr int THREADS = L * P;
   static constexpr size_t SMEM_BUF = sizeof(cpx<T>) * (size_t)N * L;
-  static constexpr size_t SMEM = SMEM_BUF * (MODE == Z_STIFF ? 4 : 1);
+  static constexpr size_t SMEM = SMEM_BUF * (MODE == Z_STIFF ? 4 : 1) + (MODE == Z_STIFF ? 256 : 0);
 };
 
 template <typename T, int N, int L, int MODE>
@@ -292,6 +395,36 @@ __global__ void __launch_bounds__(ZPass<T, N, L, MODE>::THREADS) k_z_fused(const
   auto A = [&](int k, int r) -> cpx<T>& { return Acc[((size_t)k * N + F::nat_pos(t, r)) * L + l]; };
   auto coef_pair = [&](int which, int p, long long off) -> cpx<T> {
     return ok ? S::load(a.b + ((long long)which * a.s + p) * a.nbox, off) : cmk((T)0, (T)0);
+  };
+  // compressed coefficients: class bits (2 per node: 0 outside, 1 regular,
+  // 2 irregular) of this thread's nodes, and the regular values in shared memory
+  unsigned cls[(Z::R + 7) / 8] = {};  // 4 bits per register: 2 per node of the pair
+  T* breg_s = reinterpret_cast<T*>(sm + (size_t)4 * N * L);
+  if (MODE == Z_STIFF && a.cidx) {
+    for (int j = threadIdx.x; j < 3 * a.s + 1; j += blockDim.x) breg_s[j] = a.breg[j];
+#pragma unroll
+    for (int r = 0; r < Z::R; ++r) {
+      int2 ci = make_int2(-1, -1);
+      if (ok) ci = *reinterpret_cast<const int2*>(a.cidx + base + F::nat_pos(t, r) * zs);
+      const unsigned c0 = ci.x < 0 ? 0u : (ci.x == 0 ? 1u : 2u);
+      const unsigned c1 = ci.y < 0 ? 0u : (ci.y == 0 ? 1u : 2u);
+      cls[r / 8] |= (c0 | (c1 << 2)) << (4 * (r % 8));
+    }
+  }
+  // coefficient j (b^k_p at j = k s + p, chi V at j = 3s) of the node pair at off
+  auto ccoef = [&](int r, long long off, int j) -> cpx<T> {
+    T out[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const unsigned k = (cls[r / 8] >> (4 * (r % 8) + 2 * c)) & 3u;
+      if (k == 0)
+        out[c] = (T)0;
+      else if (k == 1)
+        out[c] = breg_s[j];
+      else
+        out[c] = a.ctab[(long long)j * a.n_irr + (a.cidx[off + c] - 1)];
+    }
+    return cmk(out[0], out[1]);
   };
   cpx<T> v[Z::R], w[Z::R];
 
@@ -321,13 +454,13 @@ __global__ void __launch_bounds__(ZPass<T, N, L, MODE>::THREADS) k_z_fused(const
           if (MODE == Z_STIFF) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-              cpx<T> bk = coef_pair(1 + k, p, off);
+              cpx<T> bk = a.cidx ? ccoef(r, off, k * a.s + p) : coef_pair(1 + k, p, off);
               cpx<T>& Ak = A(k, r);
-              Ak = cmk(Ak.x + bk.x * w[r].x, Ak.y + bk.y * w[r].y);
+              Ak = pfma(bk, w[r], Ak);
             }
           } else {
             cpx<T> b0 = coef_pair(0, p, off);
-            u[r] = cmk(u[r].x + b0.x * w[r].x, u[r].y + b0.y * w[r].y);
+            u[r] = pfma(b0, w[r], u[r]);
           }
         }
       }
@@ -353,7 +486,7 @@ __global__ void __launch_bounds__(ZPass<T, N, L, MODE>::THREADS) k_z_fused(const
       cpx<T> yv = ok ? S::load(a.in1, off) : cmk((T)0, (T)0);
       if (ok && a.wfield) {
         cpx<T> wv = S::load(a.wfield, off);
-        yv = cmk(yv.x * wv.x, yv.y * wv.y);
+        yv = pmul(yv, wv);
       }
       if (ok && a.mask) yv = cmk(yv.x * (T)a.mask[off], yv.y * (T)a.mask[off + 1]);
       y[r] = yv;
@@ -370,19 +503,19 @@ __global__ void __launch_bounds__(ZPass<T, N, L, MODE>::THREADS) k_z_fused(const
         const long long off = base + F::nat_pos(t, r) * zs;
         if (MODE == Z_STIFF) {
           // g_p = chi V sum_k b^k_p A^k   (Eq. 91: C^k_p = chi V b^k_p)
-          cpx<T> cv = ok ? S::load(a.wfield, off) : cmk((T)0, (T)0);
+          cpx<T> cv = a.cidx ? ccoef(r, off, 3 * a.s) : (ok ? S::load(a.wfield, off) : cmk((T)0, (T)0));
           cpx<T> s = cmk((T)0, (T)0);
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            cpx<T> bk = coef_pair(1 + k, p, off);
+            cpx<T> bk = a.cidx ? ccoef(r, off, k * a.s + p) : coef_pair(1 + k, p, off);
             cpx<T> Ak = A(k, r);
-            s = cmk(s.x + bk.x * Ak.x, s.y + bk.y * Ak.y);
+            s = pfma(bk, Ak, s);
           }
-          v[r] = cmk(cv.x * s.x, cv.y * s.y);
+          v[r] = pmul(cv, s);
         } else {
           // g_p = w b^0_p y   (Eq. 92 with w = chi V; its transpose use with w = chi)
           cpx<T> b0 = coef_pair(0, p, off);
-          v[r] = cmk(b0.x * y[r].x, b0.y * y[r].y);
+          v[r] = pmul(b0, y[r]);
         }
       }
       F::forward(v, t, buf, a.tw);

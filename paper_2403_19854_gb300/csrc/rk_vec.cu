@@ -3,6 +3,8 @@
 #include "rk_internal.cuh"
 #include "rk_moment.cuh"
 
+#include <cstring>
+
 namespace rk {
 
 std::atomic<long long> g_launches{0};
@@ -21,6 +23,245 @@ cudaError_t launch_moment_solve(const MomentArgs& a, cudaStream_t s) {
   k_moment_solve<<<grid, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
+
+// ------------------------------------------------- coefficient compression
+__global__ void k_erode(uint8_t* out, const uint8_t* in, int axis, int r, int nx, int ny, int nz) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+    const int len = axis == 0 ? nx : (axis == 1 ? ny : nz);
+    const int c = axis == 0 ? x : (axis == 1 ? y : z);
+    const long long stride = axis == 0 ? 1 : (axis == 1 ? nx : (long long)nx * ny);
+    uint8_t ok = in[i];
+    for (int o = 1; o <= r && ok; ++o) {
+      const int cp = (c + o) % len, cm = ((c - o) % len + len) % len;
+      ok = in[i + (long long)(cp - c) * stride] && in[i + (long long)(cm - c) * stride];
+    }
+    out[i] = ok ? 1 : 0;
+  }
+}
+cudaError_t launch_erode(uint8_t* out, const uint8_t* in, int axis, int r, const int n[3], cudaStream_t s) {
+  const long long nb = ((long long)n[0] * n[1] * n[2] + 255) / 256;
+  count_launch();
+  k_erode<<<(unsigned)(nb < 152 * 32 ? nb : 152 * 32), 256, 0, s>>>(out, in, axis, r, n[0], n[1], n[2]);
+  return cudaGetLastError();
+}
+
+__global__ void k_classify(uint8_t* cls, const uint8_t* chi, const uint8_t* er, const double* V, double vreg,
+                           long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    cls[i] = !chi[i] ? 0 : ((er[i] && V[i] == vreg) ? 1 : 2);
+}
+cudaError_t launch_classify(uint8_t* cls, const uint8_t* chi, const uint8_t* eroded, const double* V, double vreg,
+                            long long n, cudaStream_t s) {
+  const long long nb = (n + 255) / 256;
+  count_launch();
+  k_classify<<<(unsigned)(nb < 152 * 32 ? nb : 152 * 32), 256, 0, s>>>(cls, chi, eroded, V, vreg, n);
+  return cudaGetLastError();
+}
+
+// block b counts the irregular nodes of [b*kScanBlock, (b+1)*kScanBlock)
+__global__ void __launch_bounds__(256) k_count_irregular(const uint8_t* cls, long long n, int* counts) {
+  __shared__ int sh[256];
+  const long long b0 = (long long)blockIdx.x * kScanBlock;
+  int c = 0;
+  for (int j = threadIdx.x; j < kScanBlock; j += 256) {
+    const long long i = b0 + j;
+    c += (i < n && cls[i] == 2) ? 1 : 0;
+  }
+  sh[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) counts[blockIdx.x] = sh[0];
+}
+cudaError_t launch_count_irregular(const uint8_t* cls, long long n, int* counts, cudaStream_t s) {
+  const long long nblk = (n + kScanBlock - 1) / kScanBlock;
+  count_launch();
+  k_count_irregular<<<(unsigned)nblk, 256, 0, s>>>(cls, n, counts);
+  return cudaGetLastError();
+}
+
+// exclusive scan of nblk counts by one block (sequential chunks, fixed order)
+__global__ void __launch_bounds__(1024) k_scan_counts(int* counts, int nblk, int* total) {
+  __shared__ int part[1024];
+  const int per = (nblk + 1023) / 1024;
+  const int b = threadIdx.x * per;
+  int sum = 0;
+  for (int j = 0; j < per && b + j < nblk; ++j) sum += counts[b + j];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int t = 0; t < 1024; ++t) {
+      const int v = part[t];
+      part[t] = run;
+      run += v;
+    }
+    *total = run;
+  }
+  __syncthreads();
+  int run = part[threadIdx.x];
+  for (int j = 0; j < per && b + j < nblk; ++j) {
+    const int v = counts[b + j];
+    counts[b + j] = run;
+    run += v;
+  }
+}
+cudaError_t launch_scan_counts(int* counts, int nblk, int* total, cudaStream_t s) {
+  count_launch();
+  k_scan_counts<<<1, 1024, 0, s>>>(counts, nblk, total);
+  return cudaGetLastError();
+}
+
+// one block per compaction block: ordered compaction of the irregular nodes
+template <typename T>
+__global__ void __launch_bounds__(256) k_compact(const uint8_t* cls, const int* offsets, long long n, int* cidx,
+                                                const T* b, int s, const T* chiV, T* tab, long long n_irr) {
+  __shared__ int sh[256];
+  const long long b0 = (long long)blockIdx.x * kScanBlock;
+  constexpr int PER = kScanBlock / 256;
+  int flags[PER];
+  int c = 0;
+  for (int j = 0; j < PER; ++j) {
+    const long long i = b0 + threadIdx.x * PER + j;
+    flags[j] = (i < n && cls[i] == 2) ? 1 : 0;
+    c += flags[j];
+  }
+  sh[threadIdx.x] = c;
+  __syncthreads();
+  // inclusive scan over the 256 thread counts (Hillis-Steele)
+  for (int o = 1; o < 256; o <<= 1) {
+    const int v = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int pos = offsets[blockIdx.x] + sh[threadIdx.x] - c;
+  const int ncoef = 3 * s + 1;
+  for (int j = 0; j < PER; ++j) {
+    const long long i = b0 + threadIdx.x * PER + j;
+    if (i >= n) break;
+    const uint8_t k = cls[i];
+    if (k == 0) {
+      cidx[i] = -1;
+    } else if (k == 1) {
+      cidx[i] = 0;
+    } else {
+      cidx[i] = 1 + pos;
+      for (int q = 0; q < 3 * s; ++q) tab[(long long)q * n_irr + pos] = b[((long long)s + q) * n + i];
+      tab[(long long)(ncoef - 1) * n_irr + pos] = chiV[i];
+      ++pos;
+    }
+  }
+}
+template <typename T>
+cudaError_t launch_compact(const uint8_t* cls, const int* offsets, long long n, int* cidx, const T* b, int s,
+                           const T* chiV, T* tab, long long n_irr, cudaStream_t st) {
+  const long long nblk = (n + kScanBlock - 1) / kScanBlock;
+  count_launch();
+  k_compact<T><<<(unsigned)nblk, 256, 0, st>>>(cls, offsets, n, cidx, b, s, chiV, tab, n_irr);
+  return cudaGetLastError();
+}
+template cudaError_t launch_compact<double>(const uint8_t*, const int*, long long, int*, const double*, int,
+                                            const double*, double*, long long, cudaStream_t);
+template cudaError_t launch_compact<float>(const uint8_t*, const int*, long long, int*, const float*, int,
+                                           const float*, float*, long long, cudaStream_t);
+
+__global__ void k_gather(double* out, const double* src, long long stride, long long idx, int count) {
+  for (int j = threadIdx.x; j < count; j += blockDim.x) out[j] = src[(long long)j * stride + idx];
+}
+cudaError_t launch_gather(double* out, const double* src, long long stride, long long idx, int count, cudaStream_t s) {
+  count_launch();
+  k_gather<<<1, 64, 0, s>>>(out, src, stride, idx, count);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------- pointwise stage of Alg. 2
+// Each thread owns VEC consecutive nodes (one 16-byte vector per field).
+template <typename T, int S>
+__global__ void __launch_bounds__(256) k_pointwise_stiff(const PointwiseArgs<T> a) {
+  constexpr int VEC = 16 / sizeof(T);
+  __shared__ T br[3 * S + 1];
+  for (int j = threadIdx.x; j < 3 * S + 1; j += blockDim.x) br[j] = a.breg[j];
+  __syncthreads();
+  const long long nv = a.nbox / VEC;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+    const long long i0 = v * VEC;
+    T d[S][VEC];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      const float4 raw = *reinterpret_cast<const float4*>(a.D[q] + i0);
+      memcpy(d[q], &raw, 16);
+    }
+    int ci[VEC];
+    if (VEC == 4) {
+      const int4 c4 = *reinterpret_cast<const int4*>(a.cidx + i0);
+      ci[0] = c4.x;
+      ci[1] = c4.y;
+      ci[VEC > 2 ? 2 : 0] = c4.z;
+      ci[VEC > 3 ? 3 : 0] = c4.w;
+    } else {
+      const int2 c2 = *reinterpret_cast<const int2*>(a.cidx + i0);
+      ci[0] = c2.x;
+      ci[1] = c2.y;
+    }
+    T g[S][VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+      const int c = ci[e];
+      T A[3] = {(T)0, (T)0, (T)0};
+      T cv = (T)0;
+      if (c == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int q = 0; q < S; ++q) A[k] += br[k * S + q] * d[q][e];
+        cv = br[3 * S];
+#pragma unroll
+        for (int p = 0; p < S; ++p) g[p][e] = cv * (br[p] * A[0] + br[S + p] * A[1] + br[2 * S + p] * A[2]);
+      } else if (c > 0) {
+        const T* row = a.ctab + (c - 1);
+        const long long ld = a.n_irr;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int q = 0; q < S; ++q) A[k] += row[(k * S + q) * ld] * d[q][e];
+        cv = row[3 * S * ld];
+#pragma unroll
+        for (int p = 0; p < S; ++p)
+          g[p][e] = cv * (row[p * ld] * A[0] + row[(S + p) * ld] * A[1] + row[(2 * S + p) * ld] * A[2]);
+      } else {
+#pragma unroll
+        for (int p = 0; p < S; ++p) g[p][e] = (T)0;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < S; ++p) {
+      float4 raw;
+      memcpy(&raw, g[p], 16);
+      *reinterpret_cast<float4*>(a.D[p] + i0) = raw;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_pointwise_stiff(const PointwiseArgs<T>& a, cudaStream_t s) {
+  constexpr int VEC = 16 / sizeof(T);
+  if (a.nbox % VEC) return cudaErrorInvalidValue;
+  const long long nb = (a.nbox / VEC + 255) / 256;
+  const unsigned grid = (unsigned)(nb < 152 * 16 ? (nb > 0 ? nb : 1) : 152 * 16);
+  count_launch();
+  if (a.s == 4)
+    k_pointwise_stiff<T, 4><<<grid, 256, 0, s>>>(a);
+  else
+    k_pointwise_stiff<T, 10><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pointwise_stiff<float>(const PointwiseArgs<float>&, cudaStream_t);
+template cudaError_t launch_pointwise_stiff<double>(const PointwiseArgs<double>&, cudaStream_t);
 
 // ----------------------------------------------------------- reductions
 // Fixed grid and fixed combination order: results are bit-reproducible.
@@ -92,6 +333,86 @@ cudaError_t launch_cg_init(const double* partials, CGState* st, cudaStream_t s) 
   k_cg_init<<<1, kRedThreads, 0, s>>>(partials, st);
   return cudaGetLastError();
 }
+
+__global__ void k_cg_set_rr(const double* part, CGState* st) {
+  const double v = reduce_partials(part);
+  if (threadIdx.x == 0) st->rr = v;
+}
+cudaError_t launch_cg_set_rr(const double* partials, CGState* st, cudaStream_t s) {
+  count_launch();
+  k_cg_set_rr<<<1, kRedThreads, 0, s>>>(partials, st);
+  return cudaGetLastError();
+}
+
+// 16-byte vectors of T (4 floats / 2 doubles)
+template <typename T>
+struct Vec16 {
+  static constexpr int N = 16 / sizeof(T);
+  T v[N];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_cg_xr_fused(T* __restrict__ x, T* __restrict__ r,
+                                                            const T* __restrict__ p, const T* __restrict__ Ap,
+                                                            CGState* st, long long n, double* __restrict__ part,
+                                                            unsigned* counter) {
+  using V = Vec16<T>;
+  const T al = (T)st->alpha;
+  double acc = 0.0;
+  const long long nv = n / V::N;
+  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < nv; i += (long long)kRedBlocks * kRedThreads) {
+    V xv = reinterpret_cast<V*>(x)[i];
+    V rv = reinterpret_cast<V*>(r)[i];
+    const V pv = reinterpret_cast<const V*>(p)[i];
+    const V av = reinterpret_cast<const V*>(Ap)[i];
+#pragma unroll
+    for (int e = 0; e < V::N; ++e) {
+      xv.v[e] += al * pv.v[e];
+      rv.v[e] -= al * av.v[e];
+      acc += (double)rv.v[e] * (double)rv.v[e];
+    }
+    reinterpret_cast<V*>(x)[i] = xv;
+    reinterpret_cast<V*>(r)[i] = rv;
+  }
+  // scalar tail (n not a multiple of the vector width)
+  for (long long i = nv * V::N + (long long)blockIdx.x * kRedThreads + threadIdx.x; i < n;
+       i += (long long)kRedBlocks * kRedThreads) {
+    x[i] += al * p[i];
+    const T ri = r[i] - al * Ap[i];
+    r[i] = ri;
+    acc += (double)ri * (double)ri;
+  }
+  acc = block_sum(acc);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = acc;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += kRedThreads) v += ((volatile double*)part)[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) {
+    st->rr_new = v;
+    st->beta = (st->rr > 0.0) ? v / st->rr : 0.0;
+    st->rr = v;
+    *counter = 0u;
+  }
+}
+template <typename T>
+cudaError_t launch_cg_xr_fused(T* x, T* r, const T* p, const T* Ap, CGState* st, long long n, double* partials,
+                               unsigned* counter, cudaStream_t s) {
+  count_launch();
+  k_cg_xr_fused<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, Ap, st, n, partials, counter);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cg_xr_fused<double>(double*, double*, const double*, const double*, CGState*, long long,
+                                                double*, unsigned*, cudaStream_t);
+template cudaError_t launch_cg_xr_fused<float>(float*, float*, const float*, const float*, CGState*, long long,
+                                               double*, unsigned*, cudaStream_t);
 
 // pAp = sum(partials); alpha = rr / pAp  (0 and flag on breakdown or rr == 0)
 __global__ void k_cg_alpha(const double* part, CGState* st) {

@@ -27,7 +27,7 @@ EXPORTED = ["rk_default_solve_opts", "rk_supported_length", "rk_setup", "rk_sing
             "rk_rhs", "rk_eval_u", "rk_eval_u_transpose", "rk_get_b", "rk_get_shape", "rk_solve",
             "rk_solve_adjoint", "rk_destroy", "rk_status_string", "rk_last_error_message",
             "rk_kernel_launches", "rk_profile_enable", "rk_profile_read", "rk_profile_class_name"]
-PROF_CLASSES = 10
+PROF_CLASSES = 11
 
 
 class RKError(RuntimeError):
