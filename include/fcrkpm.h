@@ -77,7 +77,10 @@ typedef struct rk_solve_opts {
   int32_t max_outer;  /* mixed: cap on refinement steps (default 60) */
   int32_t check_every;/* iterations between host-side convergence checks (default 25) */
   int32_t x0_given;   /* 1: on entry d holds an initial guess on the free nodes */
-  int32_t reserved;
+  int32_t fp64_finish;/* mixed: 1 (default) finishes with FP64 CG from the current iterate
+                         when the FP32 iterations stop reducing the FP64 residual (three
+                         replacements in a row without halving it, or max_outer reached);
+                         0 returns RK_ERR_NOT_CONVERGED there instead */
 } rk_solve_opts;
 
 typedef struct rk_solve_info {
@@ -90,7 +93,10 @@ typedef struct rk_solve_info {
   double setup_ms;      /* unused by rk_solve (0) */
   double solve_ms;      /* wall time of the call on the stream */
   int32_t status;       /* rk_status of the solve */
-  int32_t reserved;
+  int32_t fp64_iterations; /* FP64 CG iterations (included in iterations): all of
+                              them for RK_PREC_FP64; for mixed, those run after the
+                              FP32 iterations stopped reducing the FP64 residual
+                              (0 when the mixed scheme alone reached tol) */
 } rk_solve_info;
 
 /* Default options (tol 1e-10, mixed precision). */
@@ -185,6 +191,18 @@ rk_status rk_solve_adjoint(rk_handle* h, const double* r, const double* g, const
                            double* dJ_dr, double* dJ_dg, double* J, const rk_solve_opts* opts,
                            rk_solve_info* info, void* stream);
 
+/*
+ * rk_solve_vjp -- vector-Jacobian product of the solve map (r, g) -> u^h of
+ * rk_solve: given the cotangent u_bar of u^h, returns r_bar = (du/dr)^T u_bar and
+ * g_bar = (du/dg)^T u_bar.  The map is linear (Eq. 25, 29, 59, 62), so one adjoint
+ * solve chi_Omega K chi_Omega lambda = chi_Omega U^T (chi o u_bar) suffices:
+ * r_bar = chi V o U lambda, g_bar = chi_gamma o (U^T (chi o u_bar) - K lambda).
+ * Nothing of the forward solve is kept or needed.
+ *   u_bar, r_bar, g_bar: double[nbox].
+ */
+rk_status rk_solve_vjp(rk_handle* h, const double* u_bar, double* r_bar, double* g_bar, const rk_solve_opts* opts,
+                       rk_solve_info* info, void* stream);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 /* Kernel classes timed by rk_profile_read. */
@@ -247,6 +265,36 @@ const char* rk_profile_class_name(int32_t cls);
 #define RK_NOALLOC_MAX_DOUBLES 2105344LL
 rk_status rk_apply_K_noalloc(const rk_grid* grid, int32_t degree, double a_tilde, const uint8_t* chi,
                              const double* chiV, const double* b, const double* d, double* f, void* stream);
+
+/*
+ * rk_clone -- a handle for another right-hand side of the same domain: it shares
+ * the parent's set-up (tables, coefficients, masks -- the parent must outlive it)
+ * and owns its own workspaces and solver state, so several solves of one domain
+ * can run at the same time on different streams (rk_solve_batched).
+ */
+rk_status rk_clone(const rk_handle* parent, rk_handle** out);
+
+/* One problem of rk_solve_batched: the handle of its domain (distinct per item;
+ * use rk_clone for several right-hand sides of one domain) and the arrays of
+ * rk_solve (u may be NULL). */
+typedef struct rk_batch_item {
+  rk_handle* h;
+  const double* r;
+  const double* g;
+  double* d;
+  double* u;
+} rk_batch_item;
+
+/*
+ * rk_solve_batched -- Alg. 5 for many (domain, right-hand side) problems at once,
+ * in mixed precision.  Every item runs on its own stream (forked from `stream`);
+ * the CG iterations of all items advance together, each chunk of check_every
+ * iterations of an item being one replay of a CUDA graph captured at its first
+ * use.  Returns after every item finished; infos (NULL or n_items entries)
+ * receives each item's report.  Errors: the first failing item's status.
+ */
+rk_status rk_solve_batched(const rk_batch_item* items, int32_t n_items, const rk_solve_opts* opts,
+                           rk_solve_info* infos, void* stream);
 
 /* Release the handle and everything it owns (NULL is accepted). */
 rk_status rk_destroy(rk_handle* h);

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfcrkpm.so")
 
-SOURCES = ["rk_api.cu", "rk_vec.cu", "rk_noalloc.cu", "rk_pass_f32.cu", "rk_pass_f64.cu", "rk_z_f32.cu", "rk_z_f64.cu"]
+LENGTHS = [8, 16, 32, 36, 48, 64, 72, 96, 100, 128, 144, 162, 256]
+SOURCES = ["rk_api.cu", "rk_vec.cu", "rk_noalloc.cu", "rk_dispatch.cu"] + [f"rk_len_{n}.cu" for n in LENGTHS]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "--expt-relaxed-constexpr", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,
          "-I", CSRC] + ARCH
@@ -51,8 +52,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
+    # largest translation units first
+    order = sorted(SOURCES, key=lambda f: -int(f[7:-3]) if f.startswith("rk_len_") else 0)
     with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+        objs = list(ex.map(compile_one, order))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared"] + ARCH + ["-o", tmp] + objs + ["-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)

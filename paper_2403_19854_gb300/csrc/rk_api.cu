@@ -3,9 +3,7 @@
 // sequences the axis passes into the operators of Alg. 1-4 and runs the
 // conjugate-gradient driver of Alg. 5 (plain FP64, or FP32 inner solves inside
 // FP64 iterative refinement).
-#include <cuda.h>
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <array>
@@ -140,12 +138,6 @@ struct rk_handle {
   long long n_irr = 0;
   double breg64[31] = {};
   float breg32[31] = {};
-  // TMA descriptors of the z-pass inputs (y-pass outputs) and the device flag a
-  // timed-out tile wait sets
-  bool tma_ok = false;
-  CUtensorMap tm32[6];
-  CUtensorMap tm64[6];
-  int* err_flag = nullptr;
   // workspaces of the operator chains: X outputs, Y outputs, z-pass outputs
   double* ws64 = nullptr;
   float* ws32 = nullptr;
@@ -163,6 +155,12 @@ struct rk_handle {
   unsigned long long* counters = nullptr;  // singular count, first singular
   long long n_singular = 0, first_singular = -1;
   std::vector<void*> owned;
+  const rk_handle* parent = nullptr;  // set for clones: domain arrays belong to the parent
+  cudaStream_t bstream = nullptr;     // stream of this handle inside rk_solve_batched
+  cudaEvent_t bevent = nullptr;
+  cudaGraphExec_t chunk_graph = nullptr;  // captured chunk of FP32 CG iterations
+  int chunk_len = 0;
+  long long chunk_kernels = 0;
   // per-class kernel timing with CUDA events (rk_profile_enable)
   struct Pend {
     int cls;
@@ -731,6 +729,185 @@ rk_status cg_run(rk_handle* h, T* x, T* r, T* p, T* Ap, double rr_target, int ma
   return RK_OK;
 }
 
+// Mixed precision as a resumable job: one FP32 CG (FP32 K.u and vectors, FP64 dot
+// products) whose recurrence residual is replaced by the true FP64 residual
+// F - A64 x64 whenever it has dropped by the factor inner_tol since the last
+// replacement, after the FP32 update accumulated since then is added to the FP64
+// iterate.  The search direction is kept across replacements (the Krylov space is
+// not lost).  rk_solve runs one job to completion; rk_solve_batched interleaves
+// many, each on its own stream.
+// A residual replacement is forced after this many FP32 iterations without one, so
+// that a stagnating FP32 recurrence is noticed; kStallReplacements replacements in a
+// row that do not halve the best FP64 residual hand the solve to FP64 CG.
+constexpr int kMaxItersPerReplacement = 1000;
+constexpr int kStallReplacements = 3;
+
+struct MixedJob {
+  rk_handle* h = nullptr;
+  cudaStream_t s = nullptr;
+  rk_solve_opts o;
+  rk_solve_info* info = nullptr;
+  const double* F = nullptr;
+  double* x = nullptr;
+  double fn = 0, target = 0, rn = 0, rmax = 0, best = 0;
+  int stall = 0, it = 0, it_replaced = 0;
+  bool done = false;
+  bool use_graph = false;
+  bool fp64_tail = false;  // the mixed iterations stalled: finish in FP64
+};
+
+// r64 = F - A64 x (FP64 operator), rn = |r64|
+rk_status true_residual64(rk_handle* h, const double* F, const double* x, rk_solve_info* info, cudaStream_t s,
+                          double* rn) {
+  RK_TRY(op_K<double>(h, x, h->v64(3), h->chi_omega, h->chi_omega, s));
+  info->matvec_f64++;
+  RK_CK(launch_sub(h->v64(1), F, h->v64(3), h->nbox, s));
+  return norm2(h, h->v64(1), rn, s);
+}
+
+// j.rn holds |F - A x| for the current x (r64 = h->v64(1) holds the residual)
+rk_status mixed_start(MixedJob& j) {
+  rk_handle* h = j.h;
+  const long long n = h->nbox;
+  RK_CK(launch_to_f32(h->v32(1), h->v64(1), 1.0, n, j.s));
+  RK_CK(launch_fill<float>(h->v32(0), 0.0f, n, j.s));
+  RK_CK(launch_copy<float>(h->v32(2), h->v32(1), n, j.s));
+  RK_CK(launch_dot<float, float>(h->v32(1), h->v32(1), n, h->partials, h->dscal, j.s));
+  RK_CK(launch_cg_init(h->partials, h->cg, j.s));
+  j.rmax = j.best = j.rn;
+  j.done = j.rn <= j.target;
+  return RK_OK;
+}
+
+// one fused FP32 iteration: p = r + beta p, Ap, p.Ap -> alpha; x += alpha p, r -= alpha Ap, beta
+rk_status mixed_iteration(MixedJob& j) {
+  rk_handle* h = j.h;
+  float* x32 = h->v32(0);
+  float* r32 = h->v32(1);
+  float* p32 = h->v32(2);
+  float* Ap32 = h->v32(3);
+  const CGFuse<float> fz{p32, r32};
+  RK_TRY(op_K<float>(h, p32, Ap32, nullptr, h->chi_omega, j.s, &fz));
+  ProfScope ps(h, prof_cls<float>(RK_PROF_CG_VECTOR), j.s);
+  RK_CK(launch_cg_xr_fused<float>(x32, r32, p32, Ap32, h->cg, h->nbox, h->partials, h->counters2 + 1, j.s));
+  return RK_OK;
+}
+
+// Issue up to check_every iterations (a replayed CUDA graph when use_graph) and an
+// asynchronous copy of the CG scalars to the pinned host slot.
+rk_status mixed_issue(MixedJob& j) {
+  rk_handle* h = j.h;
+  const int k = std::min(j.o.check_every, j.o.max_iter - j.it);
+  if (k > 0) {
+    if (j.use_graph && !h->prof_on && k == j.o.check_every) {
+      if (!h->chunk_graph || h->chunk_len != k) {
+        if (h->chunk_graph) cudaGraphExecDestroy(h->chunk_graph);
+        h->chunk_graph = nullptr;
+        // this chunk runs as ordinary launches (kernel attributes get set), then the
+        // same k iterations are captured for the later chunks: the iterates do not
+        // depend on whether the handle already held a graph
+        for (int i = 0; i < k; ++i) RK_TRY(mixed_iteration(j));
+        j.info->matvec_f32 += k;
+        j.it += k;
+        const long long l0 = g_launches.load();
+        cudaGraph_t gr = nullptr;
+        RK_CK(cudaStreamBeginCapture(j.s, cudaStreamCaptureModeThreadLocal));
+        rk_status st = RK_OK;
+        for (int i = 0; i < k && st == RK_OK; ++i) st = mixed_iteration(j);
+        cudaError_t e = cudaStreamEndCapture(j.s, &gr);
+        if (st != RK_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "capture of CG iterations");
+        h->chunk_kernels = g_launches.load() - l0;
+        g_launches.fetch_sub(h->chunk_kernels);  // counted when the graph runs
+        e = cudaGraphInstantiate(&h->chunk_graph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiation");
+        h->chunk_len = k;
+        RK_CK(cudaMemcpyAsync(h->hscal, h->cg, sizeof(CGState), cudaMemcpyDeviceToHost, j.s));
+        return RK_OK;
+      }
+      RK_CK(cudaGraphLaunch(h->chunk_graph, j.s));
+      count_launch((int)h->chunk_kernels);
+      j.info->matvec_f32 += k;
+      j.it += k;
+    } else {
+      for (int i = 0; i < k; ++i) RK_TRY(mixed_iteration(j));
+      j.info->matvec_f32 += k;
+      j.it += k;
+    }
+  }
+  RK_CK(cudaMemcpyAsync(h->hscal, h->cg, sizeof(CGState), cudaMemcpyDeviceToHost, j.s));
+  return RK_OK;
+}
+
+// Wait for the scalars of the last issue; replace the residual when due.
+rk_status mixed_check(MixedJob& j) {
+  rk_handle* h = j.h;
+  const long long n = h->nbox;
+  RK_CK(cudaStreamSynchronize(j.s));
+  CGState cs;
+  memcpy(&cs, h->hscal, sizeof(CGState));
+  const double rest = std::sqrt(std::max(cs.rr, 0.0));
+  const bool cap = j.it >= j.o.max_iter;
+  const bool due = j.it - j.it_replaced >= kMaxItersPerReplacement;
+  if (!(cs.flag || rest <= j.o.inner_tol * j.rmax || rest <= 0.5 * j.target || cap || due)) return RK_OK;
+  j.it_replaced = j.it;
+  // residual replacement: x64 += x32, r64 = F - A64 x64, r32 = r64
+  RK_CK(launch_acc_f32(j.x, h->v32(0), 1.0, n, j.s));
+  RK_CK(launch_fill<float>(h->v32(0), 0.0f, n, j.s));
+  RK_TRY(true_residual64(h, j.F, j.x, j.info, j.s, &j.rn));
+  j.info->outer++;
+  if (j.rn <= j.target || cap) {
+    j.done = true;
+    return RK_OK;
+  }
+  if (j.rn < 0.5 * j.best) {
+    j.best = j.rn;
+    j.stall = 0;
+  } else if (++j.stall >= kStallReplacements || j.info->outer >= j.o.max_outer) {
+    j.done = true;  // the FP32 recurrence no longer reduces the FP64 residual
+    j.fp64_tail = true;
+    return RK_OK;
+  }
+  RK_CK(launch_to_f32(h->v32(1), h->v64(1), 1.0, n, j.s));
+  RK_CK(launch_dot<float, float>(h->v32(1), h->v32(1), n, h->partials, h->dscal, j.s));
+  if (cs.flag) {  // restart the direction after a breakdown
+    RK_CK(launch_copy<float>(h->v32(2), h->v32(1), n, j.s));
+    RK_CK(launch_cg_init(h->partials, h->cg, j.s));
+  } else {
+    RK_CK(launch_cg_set_rr(h->partials, h->cg, j.s));
+  }
+  j.rmax = j.rn;
+  return RK_OK;
+}
+
+// FP64 CG with restarts from x (r64 = h->v64(1) holds F - A x, *rn its norm) until
+// ||F - A x|| <= target or the iteration budget of o is spent; *total counts the
+// iterations already done on entry and is advanced.
+rk_status fp64_cg(rk_handle* h, const double* F, double* x, double target, const rk_solve_opts& o,
+                  rk_solve_info* info, cudaStream_t s, double* rn, int* total) {
+  for (int restart = 0; restart < 8 && *rn > target && *total < o.max_iter; ++restart) {
+    int it = 0, mv = 0;
+    double rr;
+    rk_status st = cg_run<double>(h, x, h->v64(1), h->v64(2), h->v64(3), target * target, o.max_iter - *total,
+                                  o.check_every, s, &it, &rr, &mv);
+    *total += it;
+    info->fp64_iterations += it;
+    info->matvec_f64 += mv;
+    if (st != RK_OK) return st;
+    RK_TRY(true_residual64(h, F, x, info, s, rn));
+  }
+  return RK_OK;
+}
+
+// After the mixed iterations: when the FP32 recurrence stopped reducing the FP64
+// residual (the FP32 operator cannot resolve the lowest modes once eps_32 * kappa
+// is near 1), finish with FP64 CG from the current iterate.
+rk_status mixed_finish(MixedJob& j) {
+  if (!j.fp64_tail || !j.o.fp64_finish || j.rn <= j.target) return RK_OK;
+  return fp64_cg(j.h, j.F, j.x, j.target, j.o, j.info, j.s, &j.rn, &j.it);
+}
+
 // Solve A x = F (F already masked to chi_Omega) to ||F - A x|| <= tol ||F|| with the
 // precision of opts; x holds the initial guess (masked) on entry.
 rk_status solve_masked(rk_handle* h, const double* F, double* x, const rk_solve_opts& o, rk_solve_info* info,
@@ -748,89 +925,30 @@ rk_status solve_masked(rk_handle* h, const double* F, double* x, const rk_solve_
     return RK_OK;
   }
   const double target = o.tol * fn;
-  auto true_residual = [&](double* rn) -> rk_status {
-    RK_TRY(op_K<double>(h, x, Ap64, h->chi_omega, h->chi_omega, s));
-    info->matvec_f64++;
-    RK_CK(launch_sub(r64, F, Ap64, n, s));
-    return norm2(h, r64, rn, s);
-  };
   double rn;
-  RK_TRY(true_residual(&rn));
   int total = 0;
   if (o.precision == RK_PREC_FP64) {
-    for (int restart = 0; restart < 8 && rn > target && total < o.max_iter; ++restart) {
-      int it = 0, mv = 0;
-      double rr;
-      rk_status st = cg_run<double>(h, x, r64, p64, Ap64, target * target, o.max_iter - total, o.check_every, s, &it,
-                                   &rr, &mv);
-      total += it;
-      info->matvec_f64 += mv;
-      if (st != RK_OK) {
-        info->iterations = total;
-        return st;
-      }
-      RK_TRY(true_residual(&rn));
-    }
+    RK_TRY(true_residual64(h, F, x, info, s, &rn));
+    RK_TRY(fp64_cg(h, F, x, target, o, info, s, &rn, &total));
   } else {
-    // One FP32 CG (FP32 K.u and vectors, FP64 dot products) whose recurrence
-    // residual is replaced by the true FP64 residual F - A64 x64 whenever it has
-    // dropped by the factor inner_tol since the last replacement; the FP32 update
-    // accumulated since then is added to the FP64 iterate first.  The search
-    // direction is kept across replacements, so the Krylov space is not lost.
-    float* x32 = h->v32(0);
-    float* r32 = h->v32(1);
-    float* p32 = h->v32(2);
-    float* Ap32 = h->v32(3);
-    RK_CK(launch_to_f32(r32, r64, 1.0, n, s));
-    RK_CK(launch_fill<float>(x32, 0.0f, n, s));
-    RK_CK(launch_copy<float>(p32, r32, n, s));
-    RK_CK(launch_dot<float, float>(r32, r32, n, h->partials, h->dscal, s));
-    RK_CK(launch_cg_init(h->partials, h->cg, s));
-    double rmax = rn;
-    double best = rn;
-    int stall = 0;
-    int it = 0;
-    for (;;) {
-      if (it % o.check_every == 0 || it >= o.max_iter) {
-        RK_CK(cudaMemcpyAsync(h->hscal, h->cg, sizeof(CGState), cudaMemcpyDeviceToHost, s));
-        RK_CK(cudaStreamSynchronize(s));
-        CGState cs;
-        memcpy(&cs, h->hscal, sizeof(CGState));
-        const double rest = std::sqrt(std::max(cs.rr, 0.0));
-        if (cs.flag || rest <= o.inner_tol * rmax || rest <= 0.5 * target || it >= o.max_iter) {
-          // residual replacement: x64 += x32, r64 = F - A64 x64, r32 = r64
-          RK_CK(launch_acc_f32(x, x32, 1.0, n, s));
-          RK_CK(launch_fill<float>(x32, 0.0f, n, s));
-          RK_TRY(true_residual(&rn));
-          info->outer++;
-          if (rn <= target || it >= o.max_iter) break;
-          if (rn < best) {
-            best = rn;
-            stall = 0;
-          } else if (++stall >= 4) {
-            break;  // FP32 recurrence no longer reduces the FP64 residual
-          }
-          RK_CK(launch_to_f32(r32, r64, 1.0, n, s));
-          RK_CK(launch_dot<float, float>(r32, r32, n, h->partials, h->dscal, s));
-          if (cs.flag) {  // restart the direction after a breakdown
-            RK_CK(launch_copy<float>(p32, r32, n, s));
-            RK_CK(launch_cg_init(h->partials, h->cg, s));
-          } else {
-            RK_CK(launch_cg_set_rr(h->partials, h->cg, s));
-          }
-          rmax = rn;
-        }
-      }
-      const CGFuse<float> fz{p32, r32};
-      RK_TRY(op_K<float>(h, p32, Ap32, nullptr, h->chi_omega, s, &fz));
-      info->matvec_f32++;
-      {
-        ProfScope ps(h, prof_cls<float>(RK_PROF_CG_VECTOR), s);
-        RK_CK(launch_cg_xr_fused<float>(x32, r32, p32, Ap32, h->cg, n, h->partials, h->counters2 + 1, s));
-      }
-      ++it;
+    MixedJob j;
+    j.h = h;
+    j.s = s;
+    j.o = o;
+    j.info = info;
+    j.F = F;
+    j.x = x;
+    j.fn = fn;
+    j.target = target;
+    RK_TRY(true_residual64(h, F, x, info, s, &j.rn));
+    RK_TRY(mixed_start(j));
+    while (!j.done) {
+      RK_TRY(mixed_issue(j));
+      RK_TRY(mixed_check(j));
     }
-    total = it;
+    RK_TRY(mixed_finish(j));
+    rn = j.rn;
+    total = j.it;
   }
   info->iterations = total;
   info->rel_residual = rn / fn;
@@ -846,12 +964,13 @@ void fill_defaults(rk_solve_opts* o) {
   o->max_outer = 60;
   o->check_every = 25;
   o->x0_given = 0;
-  o->reserved = 0;
+  o->fp64_finish = 1;
 }
 
 rk_status check_opts(const rk_solve_opts& o) {
   if (!(o.tol > 0.0) || o.max_iter < 1 || (o.precision != RK_PREC_FP64 && o.precision != RK_PREC_MIXED) ||
-      !(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.max_outer < 1 || o.check_every < 1)
+      !(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.max_outer < 1 || o.check_every < 1 ||
+      (o.fp64_finish != 0 && o.fp64_finish != 1))
     return fail(RK_ERR_INVALID_ARG, "invalid solve options");
   return RK_OK;
 }
@@ -882,54 +1001,6 @@ rk_status forward_solve(rk_handle* h, const double* r, const double* g, double* 
   rk_status st = solve_masked(h, F, x, o, info, s);
   RK_CK(launch_add(d, d0, x, n, s));
   return st;
-}
-
-// Tensor maps of the y-pass outputs (inputs of the fused z pass): 3D x-fastest
-// fields, box {2L, 1, n_z} = one pencil of 2L adjacent x.  Left disabled (the
-// non-TMA kernel runs) when the driver entry point or the encoding is unavailable.
-template <typename T>
-bool encode_z_maps(rk_handle* h, CUtensorMap* maps, PFN_cuTensorMapEncodeTiled_v12000 enc) {
-  for (int g = 0; g < h->chain.nY; ++g) {
-    void* addr = h->ws<T>(h->chain.nX + g);
-    cuuint64_t dims[3] = {(cuuint64_t)h->n[0], (cuuint64_t)h->n[1], (cuuint64_t)h->n[2]};
-    cuuint64_t strides[2] = {(cuuint64_t)h->n[0] * sizeof(T), (cuuint64_t)h->n[0] * h->n[1] * sizeof(T)};
-    cuuint32_t box[3] = {(cuuint32_t)(2 * z_pairs<T>()), 1u, (cuuint32_t)h->n[2]};
-    cuuint32_t estr[3] = {1u, 1u, 1u};
-    if (box[2] > 256 || (strides[0] % 16) || (strides[1] % 16)) return false;
-    CUresult r = enc(&maps[g], sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
-                     addr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return false;
-  }
-  return true;
-}
-
-rk_status setup_tma(rk_handle* h) {
-  void* fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-      q != cudaDriverEntryPointSuccess || !fn) {
-    cudaGetLastError();
-    h->tma_ok = false;
-    return RK_OK;
-  }
-  auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  RK_TRY(h->alloc(&h->err_flag, 1));
-  RK_CK(cudaMemset(h->err_flag, 0, sizeof(int)));
-  h->tma_ok = encode_z_maps<float>(h, h->tm32, enc) && encode_z_maps<double>(h, h->tm64, enc);
-  return RK_OK;
-}
-
-// RK_ERR_TIMEOUT if a bounded device wait gave up since the last check (flag cleared).
-rk_status check_device_flag(rk_handle* h) {
-  if (!h->err_flag) return RK_OK;
-  int f = 0;
-  RK_CK(cudaMemcpy(&f, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost));
-  if (f) {
-    RK_CK(cudaMemset(h->err_flag, 0, sizeof(int)));
-    return fail(RK_ERR_TIMEOUT, "a TMA tile wait of the z pass timed out");
-  }
-  return RK_OK;
 }
 
 // A node is regular when its whole support (+-reach on every axis) lies in chi and
@@ -1000,6 +1071,79 @@ rk_status compress_coefficients(rk_handle* h, cudaStream_t s) {
   return done(RK_OK);
 }
 
+// Vector-Jacobian product of the solve map (r, g) -> u^h for a cotangent e on the
+// grid (already masked by chi): w = U^T e (transpose of Alg. 3), one adjoint solve
+// A lambda = chi_Omega o w (A = chi_Omega K chi_Omega is symmetric), then
+// e_r = chi V o U lambda and e_g = chi_gamma o (w - K lambda).  The map is linear,
+// so nothing of the forward solve is needed.  e may alias e_g (it is consumed
+// first).  Solver vectors 0, 3, 4, 6 are used as scratch.
+rk_status vjp_core(rk_handle* h, const double* e, double* e_r, double* e_g, const rk_solve_opts& o,
+                   rk_solve_info* inf, cudaStream_t s) {
+  const long long n = h->nbox;
+  double* w = h->v64(6);
+  double* F = h->v64(4);
+  double* lam = h->v64(0);
+  RK_TRY(op_UT<double>(h, e, w, nullptr, h->chi, s));
+  RK_CK(launch_mask(F, w, h->chi_omega, n, s));
+  RK_CK(launch_fill<double>(lam, 0.0, n, s));
+  rk_solve_info ainf;
+  memset(&ainf, 0, sizeof(ainf));
+  rk_status st = solve_masked(h, F, lam, o, &ainf, s);
+  inf->iterations += ainf.iterations;
+  inf->outer += ainf.outer;
+  inf->matvec_f32 += ainf.matvec_f32;
+  inf->matvec_f64 += ainf.matvec_f64;
+  inf->rel_residual = std::max(inf->rel_residual, ainf.rel_residual);
+  if (st != RK_OK) return st;
+  // e_g = chi_gamma o (w - K lambda)
+  double* Klam = h->v64(3);
+  RK_TRY(op_K<double>(h, lam, Klam, h->chi, h->chi_gamma, s));
+  RK_CK(launch_masked_diff(e_g, w, Klam, h->chi_gamma, n, s));
+  // e_r = chi V o U lambda
+  RK_TRY(op_U<double>(h, lam, e_r, s));
+  RK_CK(launch_mul(e_r, h->chiV64, n, s));
+  return RK_OK;
+}
+
+// Alg. 5 "Initialize" for the batched solve: d_Gamma, F = chi_Omega (f^r - K d_Gamma),
+// x = 0, |F| and the first true residual; leaves a started mixed job.
+rk_status prepare_mixed_job(rk_handle* h, const double* r, const double* g, const rk_solve_opts& o,
+                            rk_solve_info* info, cudaStream_t s, MixedJob& j) {
+  const long long n = h->nbox;
+  double* F = h->v64(4);
+  double* d0 = h->v64(5);
+  double* t0 = h->v64(6);
+  double* x = h->v64(0);
+  if (g)
+    RK_CK(launch_dirichlet_d0(d0, g, h->chi_gamma, n, s));
+  else
+    RK_CK(launch_fill<double>(d0, 0.0, n, s));
+  RK_TRY(op_UT<double>(h, r, t0, h->chiV64, nullptr, s));
+  RK_TRY(op_K<double>(h, d0, F, h->chi, h->chi_omega, s));
+  info->matvec_f64++;
+  RK_CK(launch_masked_diff(F, t0, F, h->chi_omega, n, s));
+  RK_CK(launch_fill<double>(x, 0.0, n, s));
+  double fn;
+  RK_TRY(norm2(h, F, &fn, s));
+  info->f_norm = fn;
+  j.h = h;
+  j.s = s;
+  j.o = o;
+  j.info = info;
+  j.F = F;
+  j.x = x;
+  j.fn = fn;
+  j.target = o.tol * fn;
+  j.use_graph = true;
+  RK_CK(launch_copy<double>(h->v64(1), F, n, s));
+  j.rn = fn;  // x = 0: the residual is F
+  if (fn == 0.0) {
+    j.done = true;
+    return RK_OK;
+  }
+  return mixed_start(j);
+}
+
 }  // namespace
 
 // ======================================================================= ABI
@@ -1032,6 +1176,9 @@ rk_status rk_destroy(rk_handle* h) {
   if (!h) return RK_OK;
   prof_flush(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->chunk_graph) cudaGraphExecDestroy(h->chunk_graph);
+  if (h->bevent) cudaEventDestroy(h->bevent);
+  if (h->bstream) cudaStreamDestroy(h->bstream);
   for (void* p : h->owned) cudaFree(p);
   if (h->hscal) cudaFreeHost(h->hscal);
   delete h;
@@ -1255,11 +1402,135 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
   cudaFree(mws);
   if (st != RK_OK) return bail(st);
   if ((st = compress_coefficients(h, s)) != RK_OK) return bail(st);
-  if ((st = setup_tma(h)) != RK_OK) return bail(st);
   *out = h;
   if (h->n_singular)
     return fail(RK_ERR_SINGULAR_MOMENT,
                 std::to_string(h->n_singular) + " singular moment matrices, first at " + std::to_string(h->first_singular));
+  return RK_OK;
+}
+
+rk_status rk_clone(const rk_handle* parent, rk_handle** out) {
+  if (!parent || !out) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  rk_handle* h = new rk_handle(*parent);
+  h->owned.clear();
+  h->ev_pool.clear();
+  h->pend.clear();
+  h->prof_on = false;
+  for (int c = 0; c < 2 * RK_PROF_CLASSES; ++c) {
+    h->prof_ms[c] = 0.0;
+    h->prof_n[c] = 0;
+  }
+  h->parent = parent->parent ? parent->parent : parent;
+  h->ws64 = nullptr;
+  h->ws32 = nullptr;
+  h->sv64 = nullptr;
+  h->sv32 = nullptr;
+  h->partials = nullptr;
+  h->xpartials = nullptr;
+  h->counters2 = nullptr;
+  h->dscal = nullptr;
+  h->cg = nullptr;
+  h->hscal = nullptr;
+  for (auto& st : h->stage) st = nullptr;
+  h->bstream = nullptr;
+  h->bevent = nullptr;
+  h->chunk_graph = nullptr;
+  h->chunk_len = 0;
+  rk_status st;
+  if ((st = h->alloc(&h->ws64, (size_t)ws_fields(h->chain) * h->nbox)) != RK_OK ||
+      (st = h->alloc(&h->ws32, (size_t)ws_fields(h->chain) * h->nbox)) != RK_OK) {
+    rk_destroy(h);
+    return st;
+  }
+  *out = h;
+  return RK_OK;
+}
+
+rk_status rk_solve_batched(const rk_batch_item* items, int32_t n_items, const rk_solve_opts* opts,
+                           rk_solve_info* infos, void* stream) {
+  if (!items || n_items < 1) return fail(RK_ERR_INVALID_ARG, "no items");
+  rk_solve_opts o;
+  if (opts)
+    o = *opts;
+  else
+    fill_defaults(&o);
+  o.x0_given = 0;
+  RK_TRY(check_opts(o));
+  if (o.precision != RK_PREC_MIXED) return fail(RK_ERR_UNSUPPORTED, "batched solves run in mixed precision");
+  for (int i = 0; i < n_items; ++i) {
+    if (!items[i].h || !items[i].r || !items[i].d) return fail(RK_ERR_INVALID_ARG, "NULL item field");
+    for (int k = 0; k < i; ++k)
+      if (items[k].h == items[i].h) return fail(RK_ERR_INVALID_ARG, "items must use distinct handles (see rk_clone)");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<rk_solve_info> inf((size_t)n_items);
+  std::vector<MixedJob> jobs((size_t)n_items);
+  std::vector<Staged> sd((size_t)n_items), su((size_t)n_items);
+  cudaEvent_t fork = nullptr;
+  RK_CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  RK_CK(cudaEventRecord(fork, s));
+  rk_status first_err = RK_OK;
+  for (int i = 0; i < n_items; ++i) {
+    rk_handle* h = items[i].h;
+    memset(&inf[i], 0, sizeof(rk_solve_info));
+    RK_TRY(ensure_solver(h));
+    if (!h->bstream) RK_CK(cudaStreamCreateWithFlags(&h->bstream, cudaStreamNonBlocking));
+    if (!h->bevent) RK_CK(cudaEventCreateWithFlags(&h->bevent, cudaEventDisableTiming));
+    RK_CK(cudaStreamWaitEvent(h->bstream, fork, 0));
+    const size_t bytes = (size_t)h->nbox * 8;
+    Staged sr, sg;
+    RK_TRY(stage_in(h, 0, items[i].r, bytes, h->bstream, &sr));
+    RK_TRY(stage_in(h, 1, items[i].g, bytes, h->bstream, &sg));
+    RK_TRY(stage_out_prepare(h, 2, items[i].d, bytes, &sd[i]));
+    RK_TRY(stage_out_prepare(h, 3, items[i].u, bytes, &su[i]));
+    rk_status st = prepare_mixed_job(h, (const double*)sr.dev, (const double*)sg.dev, o, &inf[i], h->bstream, jobs[i]);
+    if (st != RK_OK) {
+      jobs[i].done = true;
+      inf[i].status = st;
+      if (first_err == RK_OK) first_err = st;
+    }
+  }
+  // all jobs advance together: issue a chunk on every active stream, then check each
+  for (;;) {
+    bool any = false;
+    for (auto& j : jobs)
+      if (!j.done) {
+        any = true;
+        RK_TRY(mixed_issue(j));
+      }
+    if (!any) break;
+    for (int i = 0; i < n_items; ++i)
+      if (!jobs[i].done) RK_TRY(mixed_check(jobs[i]));
+  }
+  for (auto& j : jobs)
+    if (j.h && inf[&j - jobs.data()].status == RK_OK) {
+      rk_status st = mixed_finish(j);
+      if (st != RK_OK) inf[&j - jobs.data()].status = st;
+    }
+  for (int i = 0; i < n_items; ++i) {
+    rk_handle* h = items[i].h;
+    MixedJob& j = jobs[i];
+    inf[i].iterations = j.it;
+    inf[i].rel_residual = j.fn > 0.0 ? j.rn / j.fn : 0.0;
+    if (inf[i].status == RK_OK && j.rn > j.target) inf[i].status = RK_ERR_NOT_CONVERGED;
+    RK_CK(launch_add((double*)sd[i].dev, h->v64(5), h->v64(0), h->nbox, h->bstream));
+    if (su[i].dev) RK_TRY(op_U<double>(h, (const double*)sd[i].dev, (double*)su[i].dev, h->bstream));
+    RK_TRY(stage_out_finish(sd[i], h->bstream));
+    RK_TRY(stage_out_finish(su[i], h->bstream));
+    RK_CK(cudaEventRecord(h->bevent, h->bstream));
+    RK_CK(cudaStreamWaitEvent(s, h->bevent, 0));
+    if (first_err == RK_OK && inf[i].status != RK_OK) first_err = (rk_status)inf[i].status;
+  }
+  RK_CK(cudaStreamSynchronize(s));
+  cudaEventDestroy(fork);
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < n_items; ++i) {
+    inf[i].solve_ms = ms;
+    if (infos) infos[i] = inf[i];
+  }
+  if (first_err != RK_OK) return fail(first_err, "at least one batched solve failed (see infos)");
   return RK_OK;
 }
 
@@ -1373,7 +1644,6 @@ rk_status rk_solve(rk_handle* h, const double* r, const double* g, double* d, do
     RK_TRY(stage_out_finish(su, s));
   }
   RK_CK(cudaStreamSynchronize(s));
-  if (st == RK_OK) st = check_device_flag(h);
   inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   inf.status = st;
   if (info) *info = inf;
@@ -1421,33 +1691,12 @@ rk_status rk_solve_adjoint(rk_handle* h, const double* r, const double* g, const
   RK_CK(launch_dot<double, double>(e, e, n, h->partials, h->dscal, s));
   RK_TRY(read_scalar(h, h->dscal, &ee, s));
   if (J) *J = 0.5 * ee;
-  // w = U^T e; adjoint solve A lambda = chi_Omega o w
-  double* w = h->v64(6);
-  double* F = h->v64(4);
-  double* lam = h->v64(0);
-  RK_TRY(op_UT<double>(h, e, w, nullptr, h->chi, s));
-  RK_CK(launch_mask(F, w, h->chi_omega, n, s));
-  RK_CK(launch_fill<double>(lam, 0.0, n, s));
-  rk_solve_info ainf;
-  memset(&ainf, 0, sizeof(ainf));
-  st = solve_masked(h, F, lam, o, &ainf, s);
-  inf.iterations += ainf.iterations;
-  inf.outer += ainf.outer;
-  inf.matvec_f32 += ainf.matvec_f32;
-  inf.matvec_f64 += ainf.matvec_f64;
-  inf.rel_residual = std::max(inf.rel_residual, ainf.rel_residual);
+  st = vjp_core(h, e, uvec, e, o, &inf, s);
   if (st != RK_OK) {
     inf.status = st;
     if (info) *info = inf;
     return st;
   }
-  // dJ/dg = chi_gamma o (w - K lambda)
-  double* Klam = h->v64(3);
-  RK_TRY(op_K<double>(h, lam, Klam, h->chi, h->chi_gamma, s));
-  RK_CK(launch_masked_diff(e, w, Klam, h->chi_gamma, n, s));
-  // dJ/dr = chi V o U lambda
-  RK_TRY(op_U<double>(h, lam, uvec, s));
-  RK_CK(launch_mul(uvec, h->chiV64, n, s));
   RK_TRY(stage_out_finish(sdr, s));
   RK_TRY(stage_out_finish(sdg, s));
   RK_CK(cudaStreamSynchronize(s));
@@ -1455,6 +1704,41 @@ rk_status rk_solve_adjoint(rk_handle* h, const double* r, const double* g, const
   inf.status = RK_OK;
   if (info) *info = inf;
   return RK_OK;
+}
+
+rk_status rk_solve_vjp(rk_handle* h, const double* u_bar, double* r_bar, double* g_bar, const rk_solve_opts* opts,
+                       rk_solve_info* info, void* stream) {
+  if (!h || !u_bar || !r_bar || !g_bar) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  rk_solve_opts o;
+  if (opts)
+    o = *opts;
+  else
+    fill_defaults(&o);
+  o.x0_given = 0;
+  RK_TRY(check_opts(o));
+  rk_solve_info inf;
+  memset(&inf, 0, sizeof(inf));
+  cudaStream_t s = (cudaStream_t)stream;
+  RK_TRY(ensure_solver(h));
+  auto t0 = std::chrono::steady_clock::now();
+  const long long n = h->nbox;
+  const size_t bytes = (size_t)n * 8;
+  Staged su, sr, sg;
+  RK_TRY(stage_in(h, 0, u_bar, bytes, s, &su));
+  RK_TRY(stage_out_prepare(h, 3, r_bar, bytes, &sr));
+  RK_TRY(stage_out_prepare(h, 4, g_bar, bytes, &sg));
+  double* e = h->v64(7);
+  RK_CK(launch_mask(e, (const double*)su.dev, h->chi, n, s));
+  rk_status st = vjp_core(h, e, (double*)sr.dev, (double*)sg.dev, o, &inf, s);
+  if (st == RK_OK) {
+    RK_TRY(stage_out_finish(sr, s));
+    RK_TRY(stage_out_finish(sg, s));
+  }
+  RK_CK(cudaStreamSynchronize(s));
+  inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  inf.status = st;
+  if (info) *info = inf;
+  return st;
 }
 
 }  // extern "C"

@@ -106,6 +106,37 @@ __device__ __forceinline__ cpx<float> pfma(cpx<float> a, cpx<float> b, cpx<float
 template <typename T>
 RK_HD cpx<T> ciscale(cpx<T> a, T s) { return cmk(-a.y * s, a.x * s); }
 
+// ------------------------------------------------------ dot-product partials
+// Per-thread partial sums of a dot product.  For double data: plain FP64 FMAs.
+// For float data the products and the running sum are kept as an unevaluated
+// pair (s + c) by the error-free transformations of Ogita, Rump and Oishi
+// ("Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005, Dot2): the
+// product error from one FMA, the addition error from Knuth's TwoSum.  The
+// partial is then as accurate as an FP64 accumulation of the same terms while
+// using FP32 instructions only (FP64 issues at a small fraction of the FP32
+// rate on this GPU).  Explicit _rn intrinsics keep the compiler from fusing
+// the product into the sum, which would break the error terms.
+template <typename T>
+struct DotAcc {
+  double s = 0.0;
+  RK_DEV void add(double a, double b) { s = fma(a, b, s); }
+  RK_DEV double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float s = 0.0f, c = 0.0f;
+  RK_DEV void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);   // a*b = p + e exactly
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);       // TwoSum: s + p = t + err exactly
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+  }
+  RK_DEV double value() const { return (double)s + (double)c; }
+};
+
 // ------------------------------------------------- compile-time trigonometry
 // cos and sin of 2*pi*m/R.  The angle is reduced exactly in integer arithmetic
 // to [0, pi/4] (octant symmetries), then evaluated with the Maclaurin series of

@@ -1,0 +1,50 @@
+// Run-time selection of the pass kernels by line length; the kernels themselves
+// are instantiated in rk_len_<N>.cu.
+#include "rk_launch.cuh"
+
+namespace rk {
+
+RK_FOR_EACH_LENGTH(RK_DECLARE_LENGTH)
+
+template <typename T>
+cudaError_t launch_split(int axis, int n, const PassArgs<T>& a, cudaStream_t s) {
+  switch (n) {
+#define RK_CASE(N) \
+  case N: return split_n<T, N>(axis, a, s);
+    RK_FOR_EACH_LENGTH(RK_CASE)
+#undef RK_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_merge(int axis, int n, const PassArgs<T>& a, cudaStream_t s) {
+  switch (n) {
+#define RK_CASE(N) \
+  case N: return merge_n<T, N>(axis, a, s);
+    RK_FOR_EACH_LENGTH(RK_CASE)
+#undef RK_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_z(int mode, int n, const ZArgs<T>& a, cudaStream_t s) {
+  switch (n) {
+#define RK_CASE(N) \
+  case N: return z_n<T, N>(mode, a, s);
+    RK_FOR_EACH_LENGTH(RK_CASE)
+#undef RK_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+
+template cudaError_t launch_split<float>(int, int, const PassArgs<float>&, cudaStream_t);
+template cudaError_t launch_split<double>(int, int, const PassArgs<double>&, cudaStream_t);
+template cudaError_t launch_merge<float>(int, int, const PassArgs<float>&, cudaStream_t);
+template cudaError_t launch_merge<double>(int, int, const PassArgs<double>&, cudaStream_t);
+template cudaError_t launch_z<float>(int, int, const ZArgs<float>&, cudaStream_t);
+template cudaError_t launch_z<double>(int, int, const ZArgs<double>&, cudaStream_t);
+
+}  // namespace rk

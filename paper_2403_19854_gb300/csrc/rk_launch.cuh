@@ -5,7 +5,6 @@
 #include <algorithm>
 
 #include "rk_internal.cuh"
-#include "rk_zpass_tma.cuh"
 
 namespace rk {
 
@@ -82,34 +81,8 @@ cudaError_t merge_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-inline int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
-  }
-  return n;
-}
-
-// persistent TMA-pipelined Z_STIFF: two resident blocks per SM
-template <typename T, int N>
-cudaError_t z_stiff_tma(const ZArgs<T>& a, cudaStream_t s) {
-  constexpr int L = Cfg<T>::LZ;
-  using Z = ZTma<T, N, L>;
-  const long long npen = (long long)((a.nx / 2 + L - 1) / L) * a.ny;
-  const long long nb = std::min<long long>(npen, 2LL * sm_count());
-  auto k = k_z_stiff_tma<T, N, L>;
-  cudaError_t e = set_smem(k, Z::SMEM);
-  if (e != cudaSuccess) return e;
-  count_launch();
-  k<<<(unsigned)nb, Z::THREADS, Z::SMEM, s>>>(a);
-  return cudaGetLastError();
-}
-
 template <typename T, int N, int MODE>
 cudaError_t z_n_mode(const ZArgs<T>& a, cudaStream_t s) {
-  if (MODE == Z_STIFF && a.use_tma && a.cidx) return z_stiff_tma<T, N>(a, s);
   constexpr int L = Cfg<T>::LZ;
   using Z = ZPass<T, N, L, MODE>;
   dim3 grid((unsigned)((a.nx / 2 + L - 1) / L), (unsigned)a.ny);
@@ -131,39 +104,24 @@ cudaError_t z_n(int mode, const ZArgs<T>& a, cudaStream_t s) {
   }
 }
 
-#define RK_FOR_EACH_LENGTH(X) X(8) X(16) X(32) X(64) X(96) X(128) X(256)
+// One translation unit per line length instantiates split_n, merge_n and z_n for
+// both precisions (rk_len_<N>.cu); rk_dispatch.cu selects them at run time.
+#define RK_FOR_EACH_LENGTH(X) X(8) X(16) X(32) X(36) X(48) X(64) X(72) X(96) X(100) X(128) X(144) X(162) X(256)
 
-template <typename T>
-cudaError_t launch_split(int axis, int n, const PassArgs<T>& a, cudaStream_t s) {
-  switch (n) {
-#define RK_CASE(N) \
-  case N: return split_n<T, N>(axis, a, s);
-    RK_FOR_EACH_LENGTH(RK_CASE)
-#undef RK_CASE
-    default: return cudaErrorInvalidValue;
-  }
-}
+#define RK_DECLARE_LENGTH(N)                                                                  \
+  extern template cudaError_t split_n<float, N>(int, const PassArgs<float>&, cudaStream_t);   \
+  extern template cudaError_t split_n<double, N>(int, const PassArgs<double>&, cudaStream_t); \
+  extern template cudaError_t merge_n<float, N>(int, const PassArgs<float>&, cudaStream_t);   \
+  extern template cudaError_t merge_n<double, N>(int, const PassArgs<double>&, cudaStream_t); \
+  extern template cudaError_t z_n<float, N>(int, const ZArgs<float>&, cudaStream_t);          \
+  extern template cudaError_t z_n<double, N>(int, const ZArgs<double>&, cudaStream_t);
 
-template <typename T>
-cudaError_t launch_merge(int axis, int n, const PassArgs<T>& a, cudaStream_t s) {
-  switch (n) {
-#define RK_CASE(N) \
-  case N: return merge_n<T, N>(axis, a, s);
-    RK_FOR_EACH_LENGTH(RK_CASE)
-#undef RK_CASE
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <typename T>
-cudaError_t launch_z(int mode, int n, const ZArgs<T>& a, cudaStream_t s) {
-  switch (n) {
-#define RK_CASE(N) \
-  case N: return z_n<T, N>(mode, a, s);
-    RK_FOR_EACH_LENGTH(RK_CASE)
-#undef RK_CASE
-    default: return cudaErrorInvalidValue;
-  }
-}
+#define RK_INSTANTIATE_LENGTH(N)                                                       \
+  template cudaError_t split_n<float, N>(int, const PassArgs<float>&, cudaStream_t);   \
+  template cudaError_t split_n<double, N>(int, const PassArgs<double>&, cudaStream_t); \
+  template cudaError_t merge_n<float, N>(int, const PassArgs<float>&, cudaStream_t);   \
+  template cudaError_t merge_n<double, N>(int, const PassArgs<double>&, cudaStream_t); \
+  template cudaError_t z_n<float, N>(int, const ZArgs<float>&, cudaStream_t);          \
+  template cudaError_t z_n<double, N>(int, const ZArgs<double>&, cudaStream_t);
 
 }  // namespace rk

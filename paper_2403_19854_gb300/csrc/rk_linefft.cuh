@@ -30,6 +30,13 @@ template <> struct LineShape<96> { static constexpr int N1 = 8, N2 = 12, P = 4; 
 template <> struct LineShape<128> { static constexpr int N1 = 8, N2 = 16, P = 8; };
 template <> struct LineShape<256> { static constexpr int N1 = 16, N2 = 16, P = 16; };
 template <> struct LineShape<512> { static constexpr int N1 = 16, N2 = 32, P = 16; };
+// 7-smooth sides used to pad uneven boxes
+template <> struct LineShape<36> { static constexpr int N1 = 6, N2 = 6, P = 6; };
+template <> struct LineShape<48> { static constexpr int N1 = 4, N2 = 12, P = 4; };
+template <> struct LineShape<72> { static constexpr int N1 = 6, N2 = 12, P = 6; };
+template <> struct LineShape<100> { static constexpr int N1 = 10, N2 = 10, P = 10; };
+template <> struct LineShape<144> { static constexpr int N1 = 12, N2 = 12, P = 12; };
+template <> struct LineShape<162> { static constexpr int N1 = 9, N2 = 18, P = 9; };
 
 template <typename T, int N>
 struct LineFFT {

@@ -22,8 +22,6 @@
 //   y and z lines: pairs of adjacent x (a float2/double2 per node pair).
 #pragma once
 
-#include <cuda.h>
-
 #include "rk_linefft.cuh"
 
 namespace rk {
@@ -183,20 +181,46 @@ RK_DEV T mask_of(const uint8_t* m, long long i) {
   return m ? (T)RK_LDG(m + i) : (T)1;
 }
 
+// The mask bytes of a block's 2*LX rows form one contiguous range (rows of
+// consecutive pairs are consecutive); copy it to shared memory with 16-byte loads
+// so the threads read their bytes from there.  Requires nx % 8 == 0 (the range
+// then starts and ends on 16-byte boundaries of the mask array).
+template <int N, int LX>
+RK_DEV void stage_mask_rows(uint8_t* dst, const uint8_t* m, long long first_row, long long nrows_total) {
+  const long long b0 = first_row * N;
+  const long long nbytes = (long long)2 * LX * N;
+  const long long avail = nrows_total * N - b0;
+  const long long lim = nbytes < avail ? nbytes : avail;
+  for (long long c = (long long)threadIdx.x * 16; c < lim; c += (long long)blockDim.x * 16)
+    *reinterpret_cast<uint4*>(dst + c) = RK_LDG(reinterpret_cast<const uint4*>(m + b0 + c));
+  RK_SYNC();
+}
+
 // p . Ap of the x MERGE epilogue: block sum in a fixed tree order, one partial
 // per block; the last block to finish sums the partials in block order (so the
 // result is reproducible), sets pAp and alpha = rr / pAp (flag on breakdown) and
 // resets the counter.
 template <int THREADS, typename T>
 __device__ __forceinline__ void cg_pap_reduce(double v, const PassArgs<T>& a) {
+  // THREADS need not be a power of two (P = 6, 9, 10, 12 threads per line): the
+  // top THREADS - POW2 values are folded onto the first ones before the tree.
+  constexpr int POW2 = THREADS >= 512 ? 512 : THREADS >= 256 ? 256 : THREADS >= 128 ? 128 : THREADS >= 64 ? 64 : 32;
+  static_assert(THREADS >= 32 && THREADS <= 1024 && THREADS < 2 * POW2, "block size");
   __shared__ double red[THREADS];
   __shared__ bool last;
+  auto tree = [&]() {
+    if (POW2 < THREADS) {
+      if ((int)threadIdx.x < THREADS - POW2) red[threadIdx.x] += red[threadIdx.x + POW2];
+      __syncthreads();
+    }
+    for (int o = POW2 / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+  };
   red[threadIdx.x] = v;
   __syncthreads();
-  for (int o = THREADS / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
+  tree();
   if (threadIdx.x == 0) {
     a.partials[blockIdx.x] = red[0];
     __threadfence();
@@ -209,10 +233,7 @@ __device__ __forceinline__ void cg_pap_reduce(double v, const PassArgs<T>& a) {
   for (unsigned b = threadIdx.x; b < gridDim.x; b += THREADS) s += ((volatile double*)a.partials)[b];
   red[threadIdx.x] = s;
   __syncthreads();
-  for (int o = THREADS / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
+  tree();
   if (threadIdx.x == 0) {
     const double pap = red[0];
     CGState* st = a.cg;
@@ -257,6 +278,15 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_split(const Pass
           a.cg_p[r1 + xp] = p1;
         }
         v[r] = cmk(p0, p1);
+      }
+    } else if (a.in_mask && N % 8 == 0) {
+      __shared__ __align__(16) uint8_t msk[2 * LX * N];
+      stage_mask_rows<N, LX>(msk, a.in_mask, 2LL * blockIdx.x * LX, (long long)a.ny * a.nz);
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) {
+        const int xp = F::nat_pos(t, r);
+        v[r] = ok ? cmk(RK_LDG(in + r0 + xp) * (T)msk[(2 * l) * N + xp], RK_LDG(in + r1 + xp) * (T)msk[(2 * l + 1) * N + xp])
+                  : cmk((T)0, (T)0);
       }
     } else {
 #pragma unroll
@@ -314,18 +344,42 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_merge(const Pass
     }
     F::inverse(acc, t, buf, a.tw);
     T* out = a.out[a.g_io[g]];
-    double dot = 0.0;
+    __shared__ __align__(16) uint8_t msk[2 * LX * N];
+    if (a.out_mask) {
+      if (N % 8 == 0) {
+        stage_mask_rows<N, LX>(msk, a.out_mask, 2LL * blockIdx.x * LX, (long long)a.ny * a.nz);
+      } else {
+        for (int j = threadIdx.x; j < 2 * LX * N; j += blockDim.x) {
+          const long long i = 2LL * blockIdx.x * LX * N + j;
+          msk[j] = i < (long long)a.ny * a.nz * N ? RK_LDG(a.out_mask + i) : (uint8_t)0;
+        }
+        RK_SYNC();
+      }
+    }
+    if (a.out_mask)
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) {
+        const int xp = F::nat_pos(t, r);
+        acc[r] = pmul(acc[r], cmk((T)msk[(2 * l) * N + xp], (T)msk[(2 * l + 1) * N + xp]));
+      }
     if (ok)
 #pragma unroll
       for (int r = 0; r < X::R; ++r) {
         const int xp = F::nat_pos(t, r);
-        const T o0 = acc[r].x * mask_of<T>(a.out_mask, r0 + xp);
-        const T o1 = acc[r].y * mask_of<T>(a.out_mask, r1 + xp);
-        out[r0 + xp] = o0;
-        out[r1 + xp] = o1;
-        if (a.cg_p) dot += (double)a.cg_p[r0 + xp] * (double)o0 + (double)a.cg_p[r1 + xp] * (double)o1;
+        out[r0 + xp] = acc[r].x;
+        out[r1 + xp] = acc[r].y;
       }
-    if (a.cg_p) cg_pap_reduce<X::THREADS>(dot, a);
+    if (a.cg_p) {
+      DotAcc<T> dot;
+      if (ok)
+#pragma unroll
+        for (int r = 0; r < X::R; ++r) {
+          const int xp = F::nat_pos(t, r);
+          dot.add(a.cg_p[r0 + xp], acc[r].x);
+          dot.add(a.cg_p[r1 + xp], acc[r].y);
+        }
+      cg_pap_reduce<X::THREADS>(dot.value(), a);
+    }
   }
 }
 
@@ -361,11 +415,6 @@ struct ZArgs {
   const T* ctab;
   long long n_irr;
   T breg[3 * 10 + 1];
-  // Z_STIFF input tiles by TMA (use_tma = 1): one tensor map per input field,
-  // box {2L, 1, N} of the x-fastest field; err receives 1 if a tile wait ran out.
-  int use_tma;
-  int* err;
-  CUtensorMap tmap[6];
 };
 
 template <typename T, int N, int L, int MODE>

@@ -11,7 +11,8 @@ std::atomic<long long> g_launches{0};
 
 bool supported_length(int n) {
   switch (n) {
-    case 8: case 16: case 32: case 64: case 96: case 128: case 256: return true;
+    case 8: case 16: case 32: case 36: case 48: case 64: case 72: case 96: case 100: case 128: case 144: case 162:
+    case 256: return true;
     default: return false;
   }
 }
@@ -289,11 +290,12 @@ __device__ __forceinline__ double block_sum(double v) {
 template <typename Ta, typename Tb>
 __global__ void __launch_bounds__(kRedThreads) k_dot(const Ta* __restrict__ a, const Tb* __restrict__ b, long long n,
                                                     double* __restrict__ part) {
-  double acc = 0.0;
+  static_assert(std::is_same<Ta, Tb>::value, "dot of equal types");
+  DotAcc<Ta> acc;
   for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads)
-    acc += (double)a[i] * (double)b[i];
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    acc.add(a[i], b[i]);
+  const double v = block_sum(acc.value());
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
 
 __device__ __forceinline__ double reduce_partials(const double* part) {
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr_fused(T* __restrict__ x, 
                                                             unsigned* counter) {
   using V = Vec16<T>;
   const T al = (T)st->alpha;
-  double acc = 0.0;
+  DotAcc<T> acc;
   const long long nv = n / V::N;
   for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < nv; i += (long long)kRedBlocks * kRedThreads) {
     V xv = reinterpret_cast<V*>(x)[i];
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr_fused(T* __restrict__ x, 
     for (int e = 0; e < V::N; ++e) {
       xv.v[e] += al * pv.v[e];
       rv.v[e] -= al * av.v[e];
-      acc += (double)rv.v[e] * (double)rv.v[e];
+      acc.add(rv.v[e], rv.v[e]);
     }
     reinterpret_cast<V*>(x)[i] = xv;
     reinterpret_cast<V*>(r)[i] = rv;
@@ -380,12 +382,12 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr_fused(T* __restrict__ x, 
     x[i] += al * p[i];
     const T ri = r[i] - al * Ap[i];
     r[i] = ri;
-    acc += (double)ri * (double)ri;
+    acc.add(ri, ri);
   }
-  acc = block_sum(acc);
+  const double bs = block_sum(acc.value());
   __shared__ bool last;
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = acc;
+    part[blockIdx.x] = bs;
     __threadfence();
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
@@ -441,15 +443,15 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr(T* __restrict__ x, T* __r
                                                       const T* __restrict__ Ap, const CGState* st, long long n,
                                                       double* __restrict__ part) {
   const T al = (T)st->alpha;
-  double acc = 0.0;
+  DotAcc<T> acc;
   for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
     x[i] += al * p[i];
     const T ri = r[i] - al * Ap[i];
     r[i] = ri;
-    acc += (double)ri * (double)ri;
+    acc.add(ri, ri);
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  const double v = block_sum(acc.value());
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
 template <typename T>
 cudaError_t launch_cg_xr(T* x, T* r, const T* p, const T* Ap, CGState* st, long long n, double* partials,

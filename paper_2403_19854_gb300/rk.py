@@ -26,7 +26,8 @@ RK_PREC_FP64, RK_PREC_MIXED = 0, 1
 EXPORTED = ["rk_default_solve_opts", "rk_supported_length", "rk_setup", "rk_singular_nodes", "rk_apply_K",
             "rk_rhs", "rk_eval_u", "rk_eval_u_transpose", "rk_get_b", "rk_get_shape", "rk_solve",
             "rk_solve_adjoint", "rk_destroy", "rk_status_string", "rk_last_error_message",
-            "rk_kernel_launches", "rk_profile_enable", "rk_profile_read", "rk_profile_class_name"]
+            "rk_kernel_launches", "rk_profile_enable", "rk_profile_read", "rk_profile_class_name",
+            "rk_solve_vjp", "rk_clone", "rk_solve_batched"]
 PROF_CLASSES = 11
 
 
@@ -43,14 +44,19 @@ class Grid(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("x0_given", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("x0_given", ctypes.c_int32), ("fp64_finish", ctypes.c_int32)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("r", ctypes.c_void_p), ("g", ctypes.c_void_p), ("d", ctypes.c_void_p),
+                ("u", ctypes.c_void_p)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("outer", ctypes.c_int32), ("matvec_f32", ctypes.c_int32),
                 ("matvec_f64", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("f_norm", ctypes.c_double),
                 ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("status", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("fp64_iterations", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -80,6 +86,10 @@ def lib():
     L.rk_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
     L.rk_solve_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    L.rk_solve_vjp.argtypes = [vp, vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    L.rk_clone.argtypes = [vp, ctypes.POINTER(vp)]
+    L.rk_solve_batched.argtypes = [ctypes.POINTER(BatchItem), i32, ctypes.POINTER(SolveOpts),
+                                   ctypes.POINTER(SolveInfo), vp]
     L.rk_destroy.argtypes = [vp]
     L.rk_status_string.argtypes = [ctypes.c_int]
     L.rk_status_string.restype = ctypes.c_char_p
@@ -197,6 +207,17 @@ class Handle:
             return cls(p.n, p.h, chi, cg, V, p.degree, p.a_tilde)
         return cls(p.n, p.h, p.chi, p.chi_gamma, p.V, p.degree, p.a_tilde)
 
+    def clone(self):
+        """A handle sharing this set-up with its own workspaces (another right-hand side)."""
+        out = ctypes.c_void_p()
+        _check(lib().rk_clone(self._h, ctypes.byref(out)))
+        c = Handle.__new__(Handle)
+        c.n, c.nbox, c.degree, c.s = self.n, self.nbox, self.degree, self.s
+        c.singular, c.setup_status = self.singular, self.setup_status
+        c._h = out
+        c._parent = self  # the parent must outlive the clone
+        return c
+
     def close(self):
         if getattr(self, "_h", None):
             lib().rk_destroy(self._h)
@@ -293,6 +314,20 @@ class Handle:
             _check(st)
         return d, u, info.as_dict()
 
+    def solve_vjp(self, u_bar, opts=None, stream=None, **kw):
+        """(r_bar, g_bar, info): vector-Jacobian product of u^h(r, g) for the cotangent u_bar."""
+        if opts is None:
+            opts = default_opts(**kw)
+        rb = _like(u_bar, RK_F64, self.nbox)
+        gb = _like(u_bar, RK_F64, self.nbox)
+        info = SolveInfo()
+        pu, ku = _ptr(u_bar)
+        pr, k1 = _ptr(rb)
+        pg, k2 = _ptr(gb)
+        _check(lib().rk_solve_vjp(self._h, pu, pr, pg, ctypes.byref(opts), ctypes.byref(info),
+                                  stream if stream is not None else _stream(u_bar)))
+        return rb, gb, info.as_dict()
+
     def solve_adjoint(self, r, g, u_target, opts=None, stream=None, **kw):
         """Gradient of J = 1/2 |u^h - u_target|^2 over chi: returns (J, dJ/dr, dJ/dg, info)."""
         if opts is None:
@@ -309,3 +344,53 @@ class Handle:
         _check(lib().rk_solve_adjoint(self._h, pr, pg, pt, pdr, pdg, ctypes.byref(J), ctypes.byref(opts),
                                       ctypes.byref(info), stream if stream is not None else _stream(r)))
         return J.value, dr, dg, info.as_dict()
+
+
+def solve_batched(items, opts=None, stream=None, raise_on_error=True, **kw):
+    """Alg. 5 for many problems at once (mixed precision).  items: sequence of
+    (handle, r, g, d, u) with distinct handles (Handle.clone() for several
+    right-hand sides of one domain); d and u are outputs (u may be None).
+    Returns the list of per-item info dicts."""
+    if opts is None:
+        opts = default_opts(**kw)
+    n = len(items)
+    arr = (BatchItem * n)()
+    keep = []
+    for i, (h, r, g, d, u) in enumerate(items):
+        pr, kr = _ptr(r)
+        pg, kg = _ptr(g)
+        pd, kd = _ptr(d)
+        pu, ku = _ptr(u)
+        keep += [kr, kg, kd, ku]
+        arr[i].h = h._h.value if isinstance(h._h, ctypes.c_void_p) else h._h
+        arr[i].r, arr[i].g, arr[i].d, arr[i].u = (pr.value if pr else None, pg.value if pg else None,
+                                                 pd.value if pd else None, pu.value if pu else None)
+    infos = (SolveInfo * n)()
+    st = lib().rk_solve_batched(arr, n, ctypes.byref(opts), infos, stream if stream is not None else _stream(items[0][1]))
+    if raise_on_error:
+        _check(st)
+    return [infos[i].as_dict() for i in range(n)]
+
+
+def poisson_solve(handle, r, g, opts=None, **kw):
+    """u^h(r, g) of Alg. 5 as a differentiable torch operation (CUDA float64 tensors).
+
+    Backward is one adjoint solve through rk_solve_vjp (the map is linear, so the
+    forward solve is recomputed from nothing and no forward state is stored)."""
+    import torch
+
+    if opts is None:
+        opts = default_opts(**kw)
+
+    class _Solve(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, r_, g_):
+            _, u, _ = handle.solve(r_.detach().contiguous(), g_.detach().contiguous(), opts=opts)
+            return u
+
+        @staticmethod
+        def backward(ctx, u_bar):
+            rb, gb, _ = handle.solve_vjp(u_bar.detach().contiguous(), opts=opts)
+            return rb, gb
+
+    return _Solve.apply(r, g)

@@ -220,3 +220,58 @@ def fourier_mode(n, kvec):
     k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     ph = 2 * np.pi * (kvec[0] * i / nx + kvec[1] * j / ny + kvec[2] * k / nz)
     return np.cos(ph).reshape(-1)
+
+
+def embed(p: Problem, n_box) -> Problem:
+    """The same problem in a larger periodic box (extra nodes outside the domain:
+    chi = 0, V = 0, r = 0, g = 0; spacing unchanged)."""
+    nb = tuple(int(v) for v in n_box)
+    if any(a < b for a, b in zip(nb, p.n)):
+        raise ValueError("box must not shrink")
+
+    def pad(a):
+        out = np.zeros((nb[2], nb[1], nb[0]), dtype=a.dtype)
+        out[:p.n[2], :p.n[1], :p.n[0]] = a.reshape(p.n[2], p.n[1], p.n[0])
+        return out.reshape(-1)
+
+    q = Problem(n=nb, h=p.h, a_tilde=p.a_tilde, degree=p.degree, chi=pad(p.chi), chi_gamma=pad(p.chi_gamma),
+                V=pad(p.V), r=pad(p.r), g=pad(p.g), u_exact=None if p.u_exact is None else pad(p.u_exact),
+                name=p.name + f"@{nb[0]}", meta=dict(p.meta))
+    q.meta["embedded_from"] = p.n
+    return q
+
+
+def gaussian_sources(n_box, h, n_gauss, rng):
+    """sum_k A_k exp(-|x - c_k|^2 / (2 s_k^2)) on the box grid, A ~ U[-1,1],
+    c ~ U[0,1]^3, s ~ U[0.05, 0.15]."""
+    nb = int(n_box)
+    x1 = np.arange(nb) * h
+    X = x1[None, None, :]
+    Y = x1[None, :, None]
+    Z = x1[:, None, None]
+    r3 = np.zeros((nb, nb, nb))
+    for _ in range(n_gauss):
+        A = rng.uniform(-1.0, 1.0)
+        c = rng.uniform(0.0, 1.0, size=3)
+        sg = rng.uniform(0.05, 0.15)
+        r3 += A * np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) / (2 * sg * sg))
+    return r3.reshape(-1)
+
+
+def batched_domains(n_domains=64, side_range=(32, 160), n_rhs=4, seed=BASE_SEED + 5000):
+    """Seeded domains of uneven size: box side S ~ U{side_range}, a union of 1..12
+    spheres (radius U[0.1, 0.3] of the unit box, h = 1/S), basis linear (a = 2.5h)
+    or quadratic (a = 3.0h) with probability 1/2, and n_rhs sources of 8 Gaussians
+    each.  Returns a list of (Problem, [r_1, ..., r_nrhs])."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_domains):
+        S = int(rng.integers(side_range[0], side_range[1] + 1))
+        deg = 1 if rng.random() < 0.5 else 2
+        a = 2.5 if deg == 1 else 3.0
+        ns = int(rng.integers(1, 13))
+        p = spheres_problem(n_box=S, n_spheres=ns, a_tilde=a, degree=deg, seed=seed + 1 + i, n_gauss=8)
+        p.name = f"batch{i}-S{S}-n{deg}"
+        rhs = [np.where(p.chi > 0, gaussian_sources(S, p.h[0], 8, rng), 0.0) for _ in range(n_rhs)]
+        out.append((p, rhs))
+    return out

@@ -1,0 +1,71 @@
+"""Adjoint gradients of J = 1/2 sum_chi (u^h - u_target)^2 on the 96^3-box cube
+(a = 2.5h, linear basis, Gaussian random source sigma = 0.1, cosine Dirichlet data).
+
+* rk_solve_adjoint against autograd through poisson_solve (rk_solve_vjp backward);
+* both against central finite differences on seeded directions: J is an exact
+  quadratic in (r, g), so (J(t + e d) - J(t - e d)) / 2e equals grad . d up to the
+  solve tolerance, for any e.
+"""
+import numpy as np
+import pytest
+
+from paper_2403_19854_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2403_19854_gb300 import rk  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def problem():
+    p = W.adjoint_problem(n_box=96, a_tilde=2.5, degree=1)
+    H = rk.Handle.from_problem(p, device=DEV)
+    t = {k: torch.as_tensor(getattr(p, k), device=DEV) for k in ("r", "g", "chi", "chi_gamma")}
+    t["ut"] = torch.as_tensor(p.meta["u_target"], device=DEV)
+    yield p, H, t
+    H.close()
+
+
+def _J(H, t, r, g, prec):
+    _, u, _ = H.solve(r, g, precision=prec, tol=1e-12)
+    e = (u - t["ut"]) * t["chi"]
+    return 0.5 * float((e * e).sum())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_adjoint_equals_autograd(problem, prec):
+    p, H, t = problem
+    J, gr, gg, info = H.solve_adjoint(t["r"], t["g"], t["ut"], precision=prec, tol=1e-12)
+    r = t["r"].clone().requires_grad_(True)
+    g = t["g"].clone().requires_grad_(True)
+    u = rk.poisson_solve(H, r, g, precision=prec, tol=1e-12)
+    e = (u - t["ut"]) * t["chi"]
+    Ja = 0.5 * (e * e).sum()
+    Ja.backward()
+    assert abs(float(Ja) - J) <= 1e-10 * J
+    assert float((r.grad - gr).norm() / gr.norm()) < 1e-8
+    assert float((g.grad - gg).norm() / gg.norm()) < 1e-8
+    # gradients vanish where the inputs are not read
+    assert float(gr[t["chi"] == 0].abs().max()) == 0.0
+    assert float(gg[t["chi_gamma"] == 0].abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_adjoint_central_differences(problem, prec):
+    p, H, t = problem
+    J, gr, gg, info = H.solve_adjoint(t["r"], t["g"], t["ut"], precision=prec, tol=1e-12)
+    rng = np.random.default_rng(20240328 + 4001)
+    for _ in range(3):
+        dr = torch.as_tensor(rng.standard_normal(p.nbox), device=DEV) * t["chi"]
+        dg = torch.as_tensor(rng.standard_normal(p.nbox), device=DEV) * t["chi_gamma"]
+        eps = 1e-3 * float(t["r"].norm()) / float(dr.norm())
+        fd = (_J(H, t, t["r"] + eps * dr, t["g"] + eps * dg, prec)
+              - _J(H, t, t["r"] - eps * dr, t["g"] - eps * dg, prec)) / (2 * eps)
+        an = float((gr * dr).sum() + (gg * dg).sum())
+        assert an == pytest.approx(fd, rel=1e-6)
