@@ -31,6 +31,39 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Persistent strided pass: as many blocks as fit on the device at once (the
+// occupancy of the kernel is queried on first use), each looping over tiles of
+// 2L x values times one index of the other axis.  a16: every row of every input
+// starts on a 16-byte boundary (16-byte async copies), else per-element copies.
+template <typename T, int N, bool MERGE>
+cudaError_t launch_strided(int axis, const PassArgs<T>& a, cudaStream_t s) {
+  constexpr int L = Cfg<T>::L;
+  using S = Strided<T, N, L>;
+  auto kernel = MERGE ? k_strided_merge<T, N, L> : k_strided_split<T, N, L>;
+  static int resident = 0;  // blocks per SM of this kernel (first device used)
+  static int sms = 0;
+  if (!resident) {
+    cudaError_t e = set_smem(kernel, S::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nb = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, S::THREADS, S::SMEM)) != cudaSuccess) return e;
+    sms = nsm;
+    resident = nb > 0 ? nb : 1;
+  }
+  const int nbx = (a.nx + S::ROW - 1) / S::ROW;
+  const long long ntiles = (long long)nbx * (axis == 1 ? a.nz : a.ny);
+  bool a16 = (a.line_stride * (long long)sizeof(T)) % 16 == 0 && (a.other_stride * (long long)sizeof(T)) % 16 == 0;
+  for (int i = 0; i < kMaxIn; ++i)
+    if (a.in[i] && (reinterpret_cast<uintptr_t>(a.in[i]) % 16) != 0) a16 = false;
+  const long long cap = (long long)resident * sms;
+  const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
+  count_launch();
+  kernel<<<grid, S::THREADS, S::SMEM, s>>>(a, nbx, ntiles, a16 ? 1 : 0);
+  return cudaGetLastError();
+}
+
 template <typename T, int N>
 cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
   if (axis == 0) {
@@ -44,14 +77,7 @@ cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
     count_launch();
     k<<<nb, X::THREADS, X::SMEM, s>>>(a);
   } else {
-    constexpr int L = Cfg<T>::L;
-    using S = Strided<T, N, L>;
-    dim3 grid((unsigned)((a.nx / 2 + L - 1) / L), (unsigned)(axis == 1 ? a.nz : a.ny));
-    auto k = k_strided_split<T, N, L>;
-    cudaError_t e = set_smem(k, S::SMEM);
-    if (e != cudaSuccess) return e;
-    count_launch();
-    k<<<grid, S::THREADS, S::SMEM, s>>>(a);
+    return launch_strided<T, N, false>(axis, a, s);
   }
   return cudaGetLastError();
 }
@@ -69,14 +95,7 @@ cudaError_t merge_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
     count_launch();
     k<<<nb, X::THREADS, X::SMEM, s>>>(a);
   } else {
-    constexpr int L = Cfg<T>::L;
-    using S = Strided<T, N, L>;
-    dim3 grid((unsigned)((a.nx / 2 + L - 1) / L), (unsigned)(axis == 1 ? a.nz : a.ny));
-    auto k = k_strided_merge<T, N, L>;
-    cudaError_t e = set_smem(k, S::SMEM);
-    if (e != cudaSuccess) return e;
-    count_launch();
-    k<<<grid, S::THREADS, S::SMEM, s>>>(a);
+    return launch_strided<T, N, true>(axis, a, s);
   }
   return cudaGetLastError();
 }

@@ -78,89 +78,183 @@ struct PassArgs {
 
 // ---------------------------------------------------------------- strided passes
 // Block: L node pairs (2L adjacent x) times P threads per line; thread (t, l) with
-// l = threadIdx.x % L fastest, so a warp reads 2L contiguous values per line
-// position.
+// l = threadIdx.x % L fastest.  A tile is the N line positions x 2L values (128
+// bytes per row) of one input field; it is copied into shared memory with
+// cp.async while the block transforms the previous tile, so the loads of the
+// next field (or of the next tile of the persistent loop) overlap the FFT work.
+
+RK_DEV void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+RK_DEV void cp_async4(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+RK_DEV void cp_async8(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+RK_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+RK_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 template <typename T, int N, int L>
 struct Strided {
   using F = LineFFT<T, N>;
-  using V2 = typename vec2<T>::type;
   static constexpr int P = F::P, R = F::R;
   static constexpr int THREADS = L * P;
-  static constexpr size_t SMEM = sizeof(cpx<T>) * (size_t)N * L;
+  // resident blocks per SM the register allocation must allow: the split pass
+  // holds one line set per thread and gains from a third block, the merge pass
+  // keeps an accumulator as well and spills at that register budget
+  static constexpr int WARP_THREADS = (THREADS + 31) / 32 * 32;
+  static constexpr int blocks_for(int threads_per_sm) {
+    return threads_per_sm / WARP_THREADS > 2 ? threads_per_sm / WARP_THREADS : 2;
+  }
+  static constexpr int MIN_BLOCKS_SPLIT = blocks_for(sizeof(T) == 4 ? 768 : 384);
+  static constexpr int MIN_BLOCKS_MERGE = blocks_for(sizeof(T) == 4 ? 512 : 384);
+  static constexpr int ROW = 2 * L;                     // values per tile row
+  static constexpr int C16 = ROW * (int)sizeof(T) / 16;  // 16-byte chunks per row
+  static constexpr size_t SMEM_BUF = sizeof(cpx<T>) * (size_t)N * L;
+  static constexpr size_t SMEM_TILE = sizeof(T) * (size_t)N * ROW;
+  static constexpr size_t SMEM = SMEM_BUF + SMEM_TILE;
 
+  // Copy rows src[x0 + j * line_stride + (0 .. nvalid-1)], j in [0, N), into tile
+  // (zero-filled beyond nvalid).  a16: every row starts on a 16-byte boundary.
+  RK_DEV static void issue(T* tile, const T* src, int nvalid, long long line_stride, bool a16) {
+    if (a16) {
+      for (int c = threadIdx.x; c < N * C16; c += THREADS) {
+        const int j = c / C16, v0 = (c % C16) * (16 / (int)sizeof(T));
+        const int bytes = max(0, min(16, (nvalid - v0) * (int)sizeof(T)));
+        cp_async16(tile + j * ROW + v0, src + (long long)j * line_stride + (bytes > 0 ? v0 : 0), bytes);
+      }
+    } else {
+      for (int c = threadIdx.x; c < N * ROW; c += THREADS) {
+        const int j = c / ROW, v = c % ROW;
+        const bool in = v < nvalid;
+        const T* g = src + (long long)j * line_stride + (in ? v : 0);
+        if (sizeof(T) == 4)
+          cp_async4(tile + j * ROW + v, g, in ? 4 : 0);
+        else
+          cp_async8(tile + j * ROW + v, g, in ? 8 : 0);
+      }
+    }
+    cp_async_commit();
+  }
   RK_DEV static cpx<T> load(const T* p, long long off) {
-    V2 v = RK_LDG(reinterpret_cast<const V2*>(p + off));
+    const typename vec2<T>::type v = RK_LDG(reinterpret_cast<const typename vec2<T>::type*>(p + off));
     return cmk(v.x, v.y);
   }
+  RK_DEV static cpx<T> at(const T* tile, int row, int l) {
+    return *reinterpret_cast<const cpx<T>*>(tile + row * ROW + 2 * l);
+  }
   RK_DEV static void store(T* p, long long off, cpx<T> v) {
-    V2 w;
+    typename vec2<T>::type w;
     w.x = v.x;
     w.y = v.y;
-    *reinterpret_cast<V2*>(p + off) = w;
+    *reinterpret_cast<typename vec2<T>::type*>(p + off) = w;
   }
 };
 
 template <typename T, int N, int L>
-__global__ void __launch_bounds__(Strided<T, N, L>::THREADS)
-    k_strided_split(const PassArgs<T> a) {
+__global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::MIN_BLOCKS_SPLIT)
+    k_strided_split(const PassArgs<T> a, const int nbx, const long long ntiles, const int a16) {
   using S = Strided<T, N, L>;
   using F = typename S::F;
   RK_DYN_SMEM(cpx<T>, sm);
+  T* tile_s = reinterpret_cast<T*>(sm + (size_t)N * L);
   const int l = threadIdx.x % L, t = threadIdx.x / L;
-  const int x = blockIdx.x * 2 * L + 2 * l;
-  const bool ok = x < a.nx;
-  const long long base = (long long)x + (long long)blockIdx.y * a.other_stride;
   InterleavedBuf<T, F::N1, F::N2> buf{sm + l, L};
+  auto origin = [&](long long tile, int* x0) -> long long {
+    *x0 = (int)(tile % nbx) * S::ROW;
+    return (long long)*x0 + (tile / nbx) * a.other_stride;
+  };
+  auto prefetch = [&](long long tile, int g) {
+    int x0;
+    const long long o = origin(tile, &x0);
+    S::issue(tile_s, a.in[a.g_io[g]] + o, a.nx - x0, a.line_stride, a16 != 0);
+  };
+  long long tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile, 0);
   cpx<T> v[S::R], w[S::R];
-  for (int g = 0; g < a.n_groups; ++g) {
-    const T* in = a.in[a.g_io[g]];
+  for (; tile < ntiles; tile += gridDim.x) {
+    int x0;
+    const long long base = origin(tile, &x0) + 2 * l;
+    const bool ok = x0 + 2 * l < a.nx;
+    for (int g = 0; g < a.n_groups; ++g) {
+      cp_async_wait_all();
+      RK_SYNC();
 #pragma unroll
-    for (int r = 0; r < S::R; ++r)
-      v[r] = ok ? S::load(in, base + F::nat_pos(t, r) * a.line_stride) : cmk((T)0, (T)0);
-    F::forward(v, t, buf, a.tw);
-    for (int q = a.g_begin[g]; q < a.g_begin[g + 1]; ++q) {
-      const int m = a.term_m[q];
+      for (int r = 0; r < S::R; ++r) v[r] = S::at(tile_s, F::nat_pos(t, r), l);
+      RK_SYNC();  // the tile is free: fetch the next field (or the first of the next tile)
+      if (g + 1 < a.n_groups)
+        prefetch(tile, g + 1);
+      else if (tile + gridDim.x < ntiles)
+        prefetch(tile + gridDim.x, 0);
+      F::forward(v, t, buf, a.tw);
+      for (int q = a.g_begin[g]; q < a.g_begin[g + 1]; ++q) {
+        const int m = a.term_m[q];
 #pragma unroll
-      for (int r = 0; r < S::R; ++r) w[r] = spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
-      F::inverse(w, t, buf, a.tw);
-      T* out = a.out[a.term_io[q]];
-      if (ok)
+        for (int r = 0; r < S::R; ++r) w[r] = spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
+        F::inverse(w, t, buf, a.tw);
+        T* out = a.out[a.term_io[q]];
+        if (ok)
 #pragma unroll
-        for (int r = 0; r < S::R; ++r) S::store(out, base + F::nat_pos(t, r) * a.line_stride, w[r]);
+          for (int r = 0; r < S::R; ++r) S::store(out, base + F::nat_pos(t, r) * a.line_stride, w[r]);
+      }
     }
   }
 }
 
 template <typename T, int N, int L>
-__global__ void __launch_bounds__(Strided<T, N, L>::THREADS)
-    k_strided_merge(const PassArgs<T> a) {
+__global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::MIN_BLOCKS_MERGE)
+    k_strided_merge(const PassArgs<T> a, const int nbx, const long long ntiles, const int a16) {
   using S = Strided<T, N, L>;
   using F = typename S::F;
   RK_DYN_SMEM(cpx<T>, sm);
+  T* tile_s = reinterpret_cast<T*>(sm + (size_t)N * L);
   const int l = threadIdx.x % L, t = threadIdx.x / L;
-  const int x = blockIdx.x * 2 * L + 2 * l;
-  const bool ok = x < a.nx;
-  const long long base = (long long)x + (long long)blockIdx.y * a.other_stride;
   InterleavedBuf<T, F::N1, F::N2> buf{sm + l, L};
+  auto origin = [&](long long tile, int* x0) -> long long {
+    *x0 = (int)(tile % nbx) * S::ROW;
+    return (long long)*x0 + (tile / nbx) * a.other_stride;
+  };
+  const int nterms = a.g_begin[a.n_groups];
+  auto prefetch = [&](long long tile, int q) {
+    int x0;
+    const long long o = origin(tile, &x0);
+    S::issue(tile_s, a.in[a.term_io[q]] + o, a.nx - x0, a.line_stride, a16 != 0);
+  };
+  long long tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile, 0);
   cpx<T> v[S::R], acc[S::R];
-  for (int g = 0; g < a.n_groups; ++g) {
+  for (; tile < ntiles; tile += gridDim.x) {
+    int x0;
+    const long long base = origin(tile, &x0) + 2 * l;
+    const bool ok = x0 + 2 * l < a.nx;
+    for (int g = 0; g < a.n_groups; ++g) {
 #pragma unroll
-    for (int r = 0; r < S::R; ++r) acc[r] = cmk((T)0, (T)0);
-    for (int q = a.g_begin[g]; q < a.g_begin[g + 1]; ++q) {
-      const T* in = a.in[a.term_io[q]];
-      const int m = a.term_m[q];
+      for (int r = 0; r < S::R; ++r) acc[r] = cmk((T)0, (T)0);
+      for (int q = a.g_begin[g]; q < a.g_begin[g + 1]; ++q) {
+        const int m = a.term_m[q];
+        cp_async_wait_all();
+        RK_SYNC();
 #pragma unroll
-      for (int r = 0; r < S::R; ++r)
-        v[r] = ok ? S::load(in, base + F::nat_pos(t, r) * a.line_stride) : cmk((T)0, (T)0);
-      F::forward(v, t, buf, a.tw);
+        for (int r = 0; r < S::R; ++r) v[r] = S::at(tile_s, F::nat_pos(t, r), l);
+        RK_SYNC();
+        if (q + 1 < nterms)
+          prefetch(tile, q + 1);
+        else if (tile + gridDim.x < ntiles)
+          prefetch(tile + gridDim.x, 0);
+        F::forward(v, t, buf, a.tw);
 #pragma unroll
-      for (int r = 0; r < S::R; ++r) acc[r] = acc[r] + spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
+        for (int r = 0; r < S::R; ++r) acc[r] = acc[r] + spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
+      }
+      F::inverse(acc, t, buf, a.tw);
+      T* out = a.out[a.g_io[g]];
+      if (ok)
+#pragma unroll
+        for (int r = 0; r < S::R; ++r) S::store(out, base + F::nat_pos(t, r) * a.line_stride, acc[r]);
     }
-    F::inverse(acc, t, buf, a.tw);
-    T* out = a.out[a.g_io[g]];
-    if (ok)
-#pragma unroll
-      for (int r = 0; r < S::R; ++r) S::store(out, base + F::nat_pos(t, r) * a.line_stride, acc[r]);
   }
 }
 
