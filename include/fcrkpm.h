@@ -50,7 +50,11 @@ typedef enum rk_status {
   RK_ERR_SINGULAR_MOMENT = 4,  /* M(x) not positive definite at some node of Omega */
   RK_ERR_NOT_CONVERGED = 5,    /* iteration cap reached before the tolerance */
   RK_ERR_BREAKDOWN = 6,        /* CG breakdown: p^T A p <= 0 or not finite */
-  RK_ERR_TIMEOUT = 7,          /* a bounded device-side wait ran out */
+  RK_ERR_TIMEOUT = 7,          /* a bounded device-side wait ran out: a y/z pass waited
+                                  too long for an input tile (TMA); the kernel gave up
+                                  and the result is invalid.  Reported by the next call
+                                  of the handle that synchronises (solves, calls with
+                                  host arrays). */
   RK_ERR_UNSUPPORTED = 8       /* grid size not built, gap too narrow, odd n[0] ... */
 } rk_status;
 

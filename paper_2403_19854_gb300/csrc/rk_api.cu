@@ -3,6 +3,8 @@
 // sequences the axis passes into the operators of Alg. 1-4 and runs the
 // conjugate-gradient driver of Alg. 5 (plain FP64, or FP32 inner solves inside
 // FP64 iterative refinement).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -150,6 +152,10 @@ struct rk_handle {
   double* dscal = nullptr;   // scratch scalars (device)
   CGState* cg = nullptr;     // device CG state
   double* hscal = nullptr;   // pinned host scalars
+  // TMA tensor maps of the workspace fields for the strided passes: [axis-1][field]
+  std::vector<CUtensorMap> tmaps32[2], tmaps64[2];
+  int* err_host = nullptr;   // mapped pinned word: a bounded device wait gave up
+  int* err_dev = nullptr;    // its device address
   // staging of host arrays
   double* stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   unsigned long long* counters = nullptr;  // singular count, first singular
@@ -291,6 +297,7 @@ template <typename T>
 PassArgs<T> pass_base(const rk_handle* h, int axis) {
   PassArgs<T> a;
   memset(&a, 0, sizeof(a));
+  a.err = h->err_dev;
   a.coef = coef_of<T>(h, axis);
   a.tw = tw_of<T>(h, axis);
   a.nx = h->n[0];
@@ -307,15 +314,44 @@ PassArgs<T> pass_base(const rk_handle* h, int axis) {
 }
 
 template <typename T>
+const std::vector<CUtensorMap>& tmaps_of(const rk_handle* h, int axis);
+template <>
+const std::vector<CUtensorMap>& tmaps_of<float>(const rk_handle* h, int axis) { return h->tmaps32[axis - 1]; }
+template <>
+const std::vector<CUtensorMap>& tmaps_of<double>(const rk_handle* h, int axis) { return h->tmaps64[axis - 1]; }
+
+// Tensor maps of the inputs of a strided pass when every input is a whole
+// workspace field with an encoded map (else false: the pass uses cp.async).
+template <typename T>
+bool tile_maps_for(rk_handle* h, int axis, const PassArgs<T>& a, TileMaps* tm) {
+  if (axis == 0) return false;
+  const std::vector<CUtensorMap>& maps = tmaps_of<T>(h, axis);
+  if (maps.empty()) return false;
+  const T* ws = h->ws<T>(0);
+  for (int i = 0; i < kMaxIn; ++i) {
+    if (!a.in[i]) continue;
+    if (i >= kMaxTma || a.in[i] < ws) return false;
+    const long long off = a.in[i] - ws;
+    if (off % h->nbox || off / h->nbox >= (long long)maps.size()) return false;
+    tm->m[i] = maps[(size_t)(off / h->nbox)];
+  }
+  return true;
+}
+
+template <typename T>
 rk_status run_split(rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s) {
   ProfScope ps(h, prof_cls<T>(axis == 0 ? RK_PROF_X_SPLIT : (axis == 1 ? RK_PROF_Y_SPLIT : RK_PROF_Z_SPLIT)), s);
-  cudaError_t e = launch_split<T>(axis, h->n[axis], a, s);
+  TileMaps tm;
+  const bool use = tile_maps_for<T>(h, axis, a, &tm);
+  cudaError_t e = launch_split<T>(axis, h->n[axis], a, s, use ? &tm : nullptr);
   return e == cudaSuccess ? RK_OK : cuda_fail(e, "split pass");
 }
 template <typename T>
 rk_status run_merge(rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s) {
   ProfScope ps(h, prof_cls<T>(axis == 0 ? RK_PROF_X_MERGE : (axis == 1 ? RK_PROF_Y_MERGE : RK_PROF_Z_MERGE)), s);
-  cudaError_t e = launch_merge<T>(axis, h->n[axis], a, s);
+  TileMaps tm;
+  const bool use = tile_maps_for<T>(h, axis, a, &tm);
+  cudaError_t e = launch_merge<T>(axis, h->n[axis], a, s, use ? &tm : nullptr);
   return e == cudaSuccess ? RK_OK : cuda_fail(e, "merge pass");
 }
 
@@ -652,6 +688,68 @@ void to_device_async(T* dst, const std::vector<T>& src, cudaStream_t s) {
   cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
 }
 
+// ------------------------------------------------------------------ TMA maps
+// Tensor maps of every workspace field for the strided y and z passes: 3D
+// x-fastest fields, box {2L, n_y, 1} (y) or {2L, 1, n_z} (z), 128-byte rows.
+// Left empty (the passes then copy tiles with cp.async) when the driver entry
+// point is unavailable or a field does not meet TMA's alignment rules (row pitch
+// a multiple of 16 bytes, line length at most 256).
+template <typename T>
+void encode_ws_maps(rk_handle* h, std::vector<CUtensorMap>* out, PFN_cuTensorMapEncodeTiled_v12000 enc) {
+  const int nf = ws_fields(h->chain);
+  constexpr int ROW = 128 / (int)sizeof(T);
+  for (int axis = 1; axis <= 2; ++axis) {
+    std::vector<CUtensorMap>& maps = out[axis - 1];
+    maps.clear();
+    cuuint64_t dims[3] = {(cuuint64_t)h->n[0], (cuuint64_t)h->n[1], (cuuint64_t)h->n[2]};
+    cuuint64_t strides[2] = {(cuuint64_t)h->n[0] * sizeof(T), (cuuint64_t)h->n[0] * h->n[1] * sizeof(T)};
+    cuuint32_t box[3] = {(cuuint32_t)ROW, axis == 1 ? (cuuint32_t)h->n[1] : 1u, axis == 2 ? (cuuint32_t)h->n[2] : 1u};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (h->n[axis] > 256 || (strides[0] % 16) || (strides[1] % 16)) continue;
+    std::vector<CUtensorMap> m((size_t)nf);
+    bool ok = true;
+    for (int f = 0; f < nf && ok; ++f) {
+      CUresult r = enc(&m[(size_t)f], sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                       3, h->ws<T>(f), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      ok = r == CUDA_SUCCESS;
+    }
+    if (ok) maps.swap(m);
+  }
+}
+
+rk_status setup_tma(rk_handle* h) {
+  if (!h->err_host) {
+    void* p = nullptr;
+    RK_CK(cudaHostAlloc(&p, sizeof(int), cudaHostAllocMapped));
+    h->err_host = (int*)p;
+    *h->err_host = 0;
+    void* d = nullptr;
+    RK_CK(cudaHostGetDevicePointer(&d, p, 0));
+    h->err_dev = (int*)d;
+  }
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return RK_OK;
+  }
+  auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  encode_ws_maps<float>(h, h->tmaps32, enc);
+  encode_ws_maps<double>(h, h->tmaps64, enc);
+  return RK_OK;
+}
+
+// RK_ERR_TIMEOUT if a bounded device wait gave up since the last check (the word
+// is cleared).  Only meaningful once the work in question has completed.
+rk_status check_device_flag(rk_handle* h) {
+  if (!h->err_host || !*(volatile int*)h->err_host) return RK_OK;
+  *(volatile int*)h->err_host = 0;
+  return fail(RK_ERR_TIMEOUT, "a bounded wait for an input tile of a strided pass gave up");
+}
+
 // ------------------------------------------------------------------ solver
 rk_status ensure_solver(rk_handle* h) {
   if (!h->sv64) RK_TRY(h->alloc(&h->sv64, (size_t)8 * h->nbox));
@@ -683,6 +781,7 @@ rk_status norm2(rk_handle* h, const double* v, double* out, cudaStream_t s) {
   RK_CK(launch_dot<double, double>(v, v, h->nbox, h->partials, h->dscal, s));
   double r2;
   RK_TRY(read_scalar(h, h->dscal, &r2, s));
+  RK_TRY(check_device_flag(h));
   *out = std::sqrt(std::max(r2, 0.0));
   return RK_OK;
 }
@@ -702,6 +801,7 @@ rk_status cg_run(rk_handle* h, T* x, T* r, T* p, T* Ap, double rr_target, int ma
     if (it % check_every == 0 || it >= max_iter) {
       RK_CK(cudaMemcpyAsync(h->hscal, h->cg, sizeof(CGState), cudaMemcpyDeviceToHost, s));
       RK_CK(cudaStreamSynchronize(s));
+      RK_TRY(check_device_flag(h));
       CGState st;
       memcpy(&st, h->hscal, sizeof(CGState));
       rr = st.rr;
@@ -845,6 +945,7 @@ rk_status mixed_check(MixedJob& j) {
   rk_handle* h = j.h;
   const long long n = h->nbox;
   RK_CK(cudaStreamSynchronize(j.s));
+  RK_TRY(check_device_flag(h));
   CGState cs;
   memcpy(&cs, h->hscal, sizeof(CGState));
   const double rest = std::sqrt(std::max(cs.rr, 0.0));
@@ -1181,6 +1282,7 @@ rk_status rk_destroy(rk_handle* h) {
   if (h->bstream) cudaStreamDestroy(h->bstream);
   for (void* p : h->owned) cudaFree(p);
   if (h->hscal) cudaFreeHost(h->hscal);
+  if (h->err_host) cudaFreeHost(h->err_host);
   delete h;
   return RK_OK;
 }
@@ -1258,6 +1360,7 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
       (st = h->alloc(&h->ws64, (size_t)ws_fields(h->chain) * n)) ||
       (st = h->alloc(&h->ws32, (size_t)ws_fields(h->chain) * n)) || (st = h->alloc(&h->counters, 2)))
     return bail(st);
+  if ((st = setup_tma(h)) != RK_OK) return bail(st);
   std::vector<uint8_t> hchi(n), hgam(n, 0), homg(n);
   cudaError_t e = cudaMemcpy(hchi.data(), chi, n, cudaMemcpyDefault);
   if (e == cudaSuccess && chi_gamma) e = cudaMemcpy(hgam.data(), chi_gamma, n, cudaMemcpyDefault);
@@ -1437,9 +1540,15 @@ rk_status rk_clone(const rk_handle* parent, rk_handle** out) {
   h->bevent = nullptr;
   h->chunk_graph = nullptr;
   h->chunk_len = 0;
+  h->err_host = nullptr;
+  h->err_dev = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    h->tmaps32[k].clear();
+    h->tmaps64[k].clear();
+  }
   rk_status st;
   if ((st = h->alloc(&h->ws64, (size_t)ws_fields(h->chain) * h->nbox)) != RK_OK ||
-      (st = h->alloc(&h->ws32, (size_t)ws_fields(h->chain) * h->nbox)) != RK_OK) {
+      (st = h->alloc(&h->ws32, (size_t)ws_fields(h->chain) * h->nbox)) != RK_OK || (st = setup_tma(h)) != RK_OK) {
     rk_destroy(h);
     return st;
   }
@@ -1525,6 +1634,11 @@ rk_status rk_solve_batched(const rk_batch_item* items, int32_t n_items, const rk
   }
   RK_CK(cudaStreamSynchronize(s));
   cudaEventDestroy(fork);
+  for (int i = 0; i < n_items; ++i)
+    if (check_device_flag(items[i].h) != RK_OK && inf[i].status == RK_OK) {
+      inf[i].status = RK_ERR_TIMEOUT;
+      if (first_err == RK_OK) first_err = RK_ERR_TIMEOUT;
+    }
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   for (int i = 0; i < n_items; ++i) {
     inf[i].solve_ms = ms;
@@ -1563,7 +1677,10 @@ rk_status rk_apply_K(rk_handle* h, const void* d, void* f, int32_t dtype, void* 
   else
     RK_TRY(op_K<float>(h, (const float*)sd.dev, (float*)sf.dev, h->chi, h->chi, s));
   RK_TRY(stage_out_finish(sf, s));
-  if (any_host({&sd, &sf})) RK_CK(cudaStreamSynchronize(s));
+  if (any_host({&sd, &sf})) {
+    RK_CK(cudaStreamSynchronize(s));
+    RK_TRY(check_device_flag(h));
+  }
   return RK_OK;
 }
 

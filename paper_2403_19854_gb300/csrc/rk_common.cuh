@@ -27,7 +27,7 @@
 // dynamic shared memory of a kernel, viewed as an array of T
 #ifndef RK_DYN_SMEM
 #define RK_DYN_SMEM(T, name)                                   \
-  extern __shared__ __align__(16) unsigned char rk_smem_raw[]; \
+  extern __shared__ __align__(128) unsigned char rk_smem_raw[]; \
   T* name = reinterpret_cast<T*>(rk_smem_raw)
 #endif
 
@@ -75,7 +75,10 @@ template <typename T>
 RK_HD cpx<T> pfma(cpx<T> a, cpx<T> b, cpx<T> c) { return cmk(a.x * b.x + c.x, a.y * b.y + c.y); }
 
 // FP32 pairs use the packed two-lane FP32 instructions of sm_100+ (one
-// instruction per component pair); other targets keep the scalar forms above.
+// instruction per component pair) where both lanes take the same operation:
+// sums, differences and lane-wise products.  Complex products stay scalar (four
+// FP32 instructions): their packed form needs lane shuffles and measured 4 %
+// slower over a K.u.  Other targets keep the scalar forms above.
 #if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
 #define RK_PACKED_F32 1
 __device__ __forceinline__ float2 rk_f2(cpx<float> a) { return make_float2(a.x, a.y); }
@@ -85,14 +88,6 @@ __device__ __forceinline__ cpx<float> operator+(cpx<float> a, cpx<float> b) {
 }
 __device__ __forceinline__ cpx<float> operator-(cpx<float> a, cpx<float> b) {
   return rk_c2(__fadd2_rn(rk_f2(a), make_float2(-b.x, -b.y)));
-}
-__device__ __forceinline__ cpx<float> cmul(cpx<float> a, cpx<float> b) {
-  // (a.x b.x - a.y b.y, a.x b.y + a.y b.x) = a.x (b.x, b.y) + a.y (-b.y, b.x)
-  return rk_c2(__ffma2_rn(make_float2(a.y, a.y), make_float2(-b.y, b.x), __fmul2_rn(make_float2(a.x, a.x), rk_f2(b))));
-}
-__device__ __forceinline__ cpx<float> cmulc(cpx<float> a, cpx<float> b) {
-  // a conj(b) = (a.x b.x + a.y b.y, a.y b.x - a.x b.y) = b.x (a.x, a.y) + b.y (a.y, -a.x)
-  return rk_c2(__ffma2_rn(make_float2(b.y, b.y), make_float2(a.y, -a.x), __fmul2_rn(make_float2(b.x, b.x), rk_f2(a))));
 }
 __device__ __forceinline__ cpx<float> cscale(cpx<float> a, float s) {
   return rk_c2(__fmul2_rn(rk_f2(a), make_float2(s, s)));

@@ -7,10 +7,10 @@ namespace rk {
 RK_FOR_EACH_LENGTH(RK_DECLARE_LENGTH)
 
 template <typename T>
-cudaError_t launch_split(int axis, int n, const PassArgs<T>& a, cudaStream_t s) {
+cudaError_t launch_split(int axis, int n, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps) {
   switch (n) {
 #define RK_CASE(N) \
-  case N: return split_n<T, N>(axis, a, s);
+  case N: return split_n<T, N>(axis, a, s, maps);
     RK_FOR_EACH_LENGTH(RK_CASE)
 #undef RK_CASE
     default: return cudaErrorInvalidValue;
@@ -18,10 +18,10 @@ cudaError_t launch_split(int axis, int n, const PassArgs<T>& a, cudaStream_t s) 
 }
 
 template <typename T>
-cudaError_t launch_merge(int axis, int n, const PassArgs<T>& a, cudaStream_t s) {
+cudaError_t launch_merge(int axis, int n, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps) {
   switch (n) {
 #define RK_CASE(N) \
-  case N: return merge_n<T, N>(axis, a, s);
+  case N: return merge_n<T, N>(axis, a, s, maps);
     RK_FOR_EACH_LENGTH(RK_CASE)
 #undef RK_CASE
     default: return cudaErrorInvalidValue;
@@ -40,10 +40,10 @@ cudaError_t launch_z(int mode, int n, const ZArgs<T>& a, cudaStream_t s) {
 }
 
 
-template cudaError_t launch_split<float>(int, int, const PassArgs<float>&, cudaStream_t);
-template cudaError_t launch_split<double>(int, int, const PassArgs<double>&, cudaStream_t);
-template cudaError_t launch_merge<float>(int, int, const PassArgs<float>&, cudaStream_t);
-template cudaError_t launch_merge<double>(int, int, const PassArgs<double>&, cudaStream_t);
+template cudaError_t launch_split<float>(int, int, const PassArgs<float>&, cudaStream_t, const TileMaps*);
+template cudaError_t launch_split<double>(int, int, const PassArgs<double>&, cudaStream_t, const TileMaps*);
+template cudaError_t launch_merge<float>(int, int, const PassArgs<float>&, cudaStream_t, const TileMaps*);
+template cudaError_t launch_merge<double>(int, int, const PassArgs<double>&, cudaStream_t, const TileMaps*);
 template cudaError_t launch_z<float>(int, int, const ZArgs<float>&, cudaStream_t);
 template cudaError_t launch_z<double>(int, int, const ZArgs<double>&, cudaStream_t);
 

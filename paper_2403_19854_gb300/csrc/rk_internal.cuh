@@ -25,9 +25,9 @@ bool supported_length(int n);
 
 // axis: 0 = x (contiguous lines), 1 = y, 2 = z (strided lines)
 template <typename T>
-cudaError_t launch_split(int axis, int n, const PassArgs<T>& a, cudaStream_t s);
+cudaError_t launch_split(int axis, int n, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps = nullptr);
 template <typename T>
-cudaError_t launch_merge(int axis, int n, const PassArgs<T>& a, cudaStream_t s);
+cudaError_t launch_merge(int axis, int n, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps = nullptr);
 template <typename T>
 cudaError_t launch_z(int mode, int n, const ZArgs<T>& a, cudaStream_t s);
 

@@ -36,7 +36,7 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
 // 2L x values times one index of the other axis.  a16: every row of every input
 // starts on a 16-byte boundary (16-byte async copies), else per-element copies.
 template <typename T, int N, bool MERGE>
-cudaError_t launch_strided(int axis, const PassArgs<T>& a, cudaStream_t s) {
+cudaError_t launch_strided(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps) {
   constexpr int L = Cfg<T>::L;
   using S = Strided<T, N, L>;
   auto kernel = MERGE ? k_strided_merge<T, N, L> : k_strided_split<T, N, L>;
@@ -59,13 +59,14 @@ cudaError_t launch_strided(int axis, const PassArgs<T>& a, cudaStream_t s) {
     if (a.in[i] && (reinterpret_cast<uintptr_t>(a.in[i]) % 16) != 0) a16 = false;
   const long long cap = (long long)resident * sms;
   const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
+  static const TileMaps none = {};
   count_launch();
-  kernel<<<grid, S::THREADS, S::SMEM, s>>>(a, nbx, ntiles, a16 ? 1 : 0);
+  kernel<<<grid, S::THREADS, S::SMEM, s>>>(a, nbx, ntiles, a16 ? 1 : 0, maps ? *maps : none, maps ? axis : 0);
   return cudaGetLastError();
 }
 
 template <typename T, int N>
-cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
+cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps) {
   if (axis == 0) {
     constexpr int LX = Cfg<T>::XTHREADS / LineShape<N>::P;
     using X = XPass<T, N, LX>;
@@ -77,13 +78,13 @@ cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
     count_launch();
     k<<<nb, X::THREADS, X::SMEM, s>>>(a);
   } else {
-    return launch_strided<T, N, false>(axis, a, s);
+    return launch_strided<T, N, false>(axis, a, s, maps);
   }
   return cudaGetLastError();
 }
 
 template <typename T, int N>
-cudaError_t merge_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
+cudaError_t merge_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps) {
   if (axis == 0) {
     constexpr int LX = Cfg<T>::XTHREADS / LineShape<N>::P;
     using X = XPass<T, N, LX>;
@@ -95,7 +96,7 @@ cudaError_t merge_n(int axis, const PassArgs<T>& a, cudaStream_t s) {
     count_launch();
     k<<<nb, X::THREADS, X::SMEM, s>>>(a);
   } else {
-    return launch_strided<T, N, true>(axis, a, s);
+    return launch_strided<T, N, true>(axis, a, s, maps);
   }
   return cudaGetLastError();
 }
@@ -128,18 +129,18 @@ cudaError_t z_n(int mode, const ZArgs<T>& a, cudaStream_t s) {
 #define RK_FOR_EACH_LENGTH(X) X(8) X(16) X(32) X(36) X(48) X(64) X(72) X(96) X(100) X(128) X(144) X(162) X(256)
 
 #define RK_DECLARE_LENGTH(N)                                                                  \
-  extern template cudaError_t split_n<float, N>(int, const PassArgs<float>&, cudaStream_t);   \
-  extern template cudaError_t split_n<double, N>(int, const PassArgs<double>&, cudaStream_t); \
-  extern template cudaError_t merge_n<float, N>(int, const PassArgs<float>&, cudaStream_t);   \
-  extern template cudaError_t merge_n<double, N>(int, const PassArgs<double>&, cudaStream_t); \
+  extern template cudaError_t split_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*);   \
+  extern template cudaError_t split_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*); \
+  extern template cudaError_t merge_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*);   \
+  extern template cudaError_t merge_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*); \
   extern template cudaError_t z_n<float, N>(int, const ZArgs<float>&, cudaStream_t);          \
   extern template cudaError_t z_n<double, N>(int, const ZArgs<double>&, cudaStream_t);
 
 #define RK_INSTANTIATE_LENGTH(N)                                                       \
-  template cudaError_t split_n<float, N>(int, const PassArgs<float>&, cudaStream_t);   \
-  template cudaError_t split_n<double, N>(int, const PassArgs<double>&, cudaStream_t); \
-  template cudaError_t merge_n<float, N>(int, const PassArgs<float>&, cudaStream_t);   \
-  template cudaError_t merge_n<double, N>(int, const PassArgs<double>&, cudaStream_t); \
+  template cudaError_t split_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*);   \
+  template cudaError_t split_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*); \
+  template cudaError_t merge_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*);   \
+  template cudaError_t merge_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*); \
   template cudaError_t z_n<float, N>(int, const ZArgs<float>&, cudaStream_t);          \
   template cudaError_t z_n<double, N>(int, const ZArgs<double>&, cudaStream_t);
 

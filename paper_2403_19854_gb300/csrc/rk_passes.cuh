@@ -23,6 +23,7 @@
 #pragma once
 
 #include "rk_linefft.cuh"
+#include "rk_tma.cuh"
 
 namespace rk {
 
@@ -74,6 +75,7 @@ struct PassArgs {
   CGState* cg;                // beta (read); pAp, alpha, flag (written by the last MERGE block)
   double* partials;           // MERGE: one partial p.Ap per block
   unsigned* counter;          // MERGE: blocks finished (the last one reduces and resets it)
+  int* err;                   // set to 1 when a bounded wait for an input tile gave up
 };
 
 // ---------------------------------------------------------------- strided passes
@@ -155,36 +157,87 @@ struct Strided {
   }
 };
 
+// Tile feed of a strided pass.  tma_axis 1 or 2: the tiles are TMA boxes of the
+// inputs' tensor maps ({2L, N, 1} at (x0, 0, other) along y, {2L, 1, N} at
+// (x0, other, 0) along z), completed on one mbarrier; tma_axis 0: cp.async.
+template <typename T, int N, int L>
+struct TileFeed {
+  using S = Strided<T, N, L>;
+  T* tile;
+  uint64_t* bar;
+  uint32_t phase;
+  int tma_axis;
+  RK_DEV void init() {
+    if (tma_axis) {
+      if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+      }
+      RK_SYNC();
+    }
+  }
+  // start the copy of input `which` (pointer src = field + origin) of the tile at (x0, other)
+  RK_DEV void issue(const TileMaps& maps, int which, const T* src, int x0, int other, int nx, long long line_stride,
+                    bool a16) {
+    if (tma_axis) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, (uint32_t)S::SMEM_TILE);
+        tma_load_3d(tile, &maps.m[which], bar, x0, tma_axis == 1 ? 0 : other, tma_axis == 1 ? other : 0);
+      }
+    } else {
+      S::issue(tile, src, nx - x0, line_stride, a16);
+    }
+  }
+  // wait for the tile; false (uniformly over the block) if the bounded wait gave up,
+  // after which the caller returns
+  RK_DEV bool wait(int* err) {
+    bool ok = true;
+    if (tma_axis) {
+      ok = mbar_wait(bar, phase);
+      phase ^= 1u;
+    } else {
+      cp_async_wait_all();
+    }
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0 && err) atomicExch(err, 1);
+      if (tma_axis) mbar_wait(bar, phase ^ 1u);  // the copy still in flight, bounded
+      return false;
+    }
+    return true;
+  }
+};
+
 template <typename T, int N, int L>
 __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::MIN_BLOCKS_SPLIT)
-    k_strided_split(const PassArgs<T> a, const int nbx, const long long ntiles, const int a16) {
+    k_strided_split(const PassArgs<T> a, const int nbx, const long long ntiles, const int a16,
+                    const __grid_constant__ TileMaps maps, const int tma_axis) {
   using S = Strided<T, N, L>;
   using F = typename S::F;
-  RK_DYN_SMEM(cpx<T>, sm);
-  T* tile_s = reinterpret_cast<T*>(sm + (size_t)N * L);
+  RK_DYN_SMEM(unsigned char, smem);
+  __shared__ uint64_t bar;
+  TileFeed<T, N, L> feed{reinterpret_cast<T*>(smem), &bar, 0u, tma_axis};
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem + S::SMEM_TILE);
   const int l = threadIdx.x % L, t = threadIdx.x / L;
   InterleavedBuf<T, F::N1, F::N2> buf{sm + l, L};
-  auto origin = [&](long long tile, int* x0) -> long long {
-    *x0 = (int)(tile % nbx) * S::ROW;
-    return (long long)*x0 + (tile / nbx) * a.other_stride;
-  };
+  feed.init();
   auto prefetch = [&](long long tile, int g) {
-    int x0;
-    const long long o = origin(tile, &x0);
-    S::issue(tile_s, a.in[a.g_io[g]] + o, a.nx - x0, a.line_stride, a16 != 0);
+    const int x0 = (int)(tile % nbx) * S::ROW;
+    const long long by = tile / nbx;
+    const int in = a.g_io[g];
+    feed.issue(maps, in, a.in[in] + x0 + by * a.other_stride, x0, (int)by, a.nx, a.line_stride, a16 != 0);
   };
   long long tile = blockIdx.x;
   if (tile < ntiles) prefetch(tile, 0);
   cpx<T> v[S::R], w[S::R];
   for (; tile < ntiles; tile += gridDim.x) {
-    int x0;
-    const long long base = origin(tile, &x0) + 2 * l;
+    const int x0 = (int)(tile % nbx) * S::ROW;
+    const long long base = x0 + (tile / nbx) * a.other_stride + 2 * l;
     const bool ok = x0 + 2 * l < a.nx;
     for (int g = 0; g < a.n_groups; ++g) {
-      cp_async_wait_all();
-      RK_SYNC();
+      if (!feed.wait(a.err)) return;
 #pragma unroll
-      for (int r = 0; r < S::R; ++r) v[r] = S::at(tile_s, F::nat_pos(t, r), l);
+      for (int r = 0; r < S::R; ++r) v[r] = S::at(feed.tile, F::nat_pos(t, r), l);
       RK_SYNC();  // the tile is free: fetch the next field (or the first of the next tile)
       if (g + 1 < a.n_groups)
         prefetch(tile, g + 1);
@@ -207,39 +260,39 @@ __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::M
 
 template <typename T, int N, int L>
 __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::MIN_BLOCKS_MERGE)
-    k_strided_merge(const PassArgs<T> a, const int nbx, const long long ntiles, const int a16) {
+    k_strided_merge(const PassArgs<T> a, const int nbx, const long long ntiles, const int a16,
+                    const __grid_constant__ TileMaps maps, const int tma_axis) {
   using S = Strided<T, N, L>;
   using F = typename S::F;
-  RK_DYN_SMEM(cpx<T>, sm);
-  T* tile_s = reinterpret_cast<T*>(sm + (size_t)N * L);
+  RK_DYN_SMEM(unsigned char, smem);
+  __shared__ uint64_t bar;
+  TileFeed<T, N, L> feed{reinterpret_cast<T*>(smem), &bar, 0u, tma_axis};
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem + S::SMEM_TILE);
   const int l = threadIdx.x % L, t = threadIdx.x / L;
   InterleavedBuf<T, F::N1, F::N2> buf{sm + l, L};
-  auto origin = [&](long long tile, int* x0) -> long long {
-    *x0 = (int)(tile % nbx) * S::ROW;
-    return (long long)*x0 + (tile / nbx) * a.other_stride;
-  };
+  feed.init();
   const int nterms = a.g_begin[a.n_groups];
   auto prefetch = [&](long long tile, int q) {
-    int x0;
-    const long long o = origin(tile, &x0);
-    S::issue(tile_s, a.in[a.term_io[q]] + o, a.nx - x0, a.line_stride, a16 != 0);
+    const int x0 = (int)(tile % nbx) * S::ROW;
+    const long long by = tile / nbx;
+    const int in = a.term_io[q];
+    feed.issue(maps, in, a.in[in] + x0 + by * a.other_stride, x0, (int)by, a.nx, a.line_stride, a16 != 0);
   };
   long long tile = blockIdx.x;
   if (tile < ntiles) prefetch(tile, 0);
   cpx<T> v[S::R], acc[S::R];
   for (; tile < ntiles; tile += gridDim.x) {
-    int x0;
-    const long long base = origin(tile, &x0) + 2 * l;
+    const int x0 = (int)(tile % nbx) * S::ROW;
+    const long long base = x0 + (tile / nbx) * a.other_stride + 2 * l;
     const bool ok = x0 + 2 * l < a.nx;
     for (int g = 0; g < a.n_groups; ++g) {
 #pragma unroll
       for (int r = 0; r < S::R; ++r) acc[r] = cmk((T)0, (T)0);
       for (int q = a.g_begin[g]; q < a.g_begin[g + 1]; ++q) {
         const int m = a.term_m[q];
-        cp_async_wait_all();
-        RK_SYNC();
+        if (!feed.wait(a.err)) return;
 #pragma unroll
-        for (int r = 0; r < S::R; ++r) v[r] = S::at(tile_s, F::nat_pos(t, r), l);
+        for (int r = 0; r < S::R; ++r) v[r] = S::at(feed.tile, F::nat_pos(t, r), l);
         RK_SYNC();
         if (q + 1 < nterms)
           prefetch(tile, q + 1);
