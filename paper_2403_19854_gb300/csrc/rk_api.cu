@@ -1150,8 +1150,9 @@ rk_status compress_coefficients(rk_handle* h, cudaStream_t s) {
   h->n_irr = total;
   const int ncoef = 3 * h->s + 1;
   rk_status st;
-  if ((st = h->alloc(&h->cidx, (size_t)n)) != RK_OK || (st = h->alloc(&h->ctab64, (size_t)ncoef * total)) != RK_OK ||
-      (st = h->alloc(&h->ctab32, (size_t)ncoef * total)) != RK_OK)
+  if ((st = h->alloc(&h->cidx, (size_t)n)) != RK_OK ||
+      (st = h->alloc(&h->ctab64, (size_t)ctab_pitch<double>(h->s) * total)) != RK_OK ||
+      (st = h->alloc(&h->ctab32, (size_t)ctab_pitch<float>(h->s) * total)) != RK_OK)
     return done(st);
   if ((e = launch_compact<double>(cls, counts, n, h->cidx, h->b64, h->s, h->chiV64, h->ctab64, total, s)) !=
           cudaSuccess ||

@@ -132,6 +132,37 @@ struct DotAcc<float> {
   RK_DEV double value() const { return (double)s + (double)c; }
 };
 
+// Two partials in one: the component pairs a thread holds (two lines, two
+// nodes) accumulate lane by lane, which for FP32 on sm_100+ runs the same
+// compensated steps as DotAcc<float> in packed two-lane instructions.
+template <typename T>
+struct DotAccPair {
+  DotAcc<T> d;
+  RK_DEV void add(cpx<T> a, cpx<T> b) {
+    d.add(a.x, b.x);
+    d.add(a.y, b.y);
+  }
+  RK_DEV double value() const { return d.value(); }
+};
+#if defined(RK_PACKED_F32)
+template <>
+struct DotAccPair<float> {
+  float2 s = make_float2(0.0f, 0.0f), c = make_float2(0.0f, 0.0f);
+  static RK_DEV float2 neg(float2 v) { return make_float2(-v.x, -v.y); }
+  RK_DEV void add(cpx<float> a, cpx<float> b) {
+    const float2 fa = rk_f2(a), fb = rk_f2(b);
+    const float2 p = __fmul2_rn(fa, fb);
+    const float2 e = __ffma2_rn(fa, fb, neg(p));
+    const float2 t = __fadd2_rn(s, p);
+    const float2 z = __fadd2_rn(t, neg(s));
+    const float2 err = __fadd2_rn(__fadd2_rn(s, neg(__fadd2_rn(t, neg(z)))), __fadd2_rn(p, neg(z)));
+    s = t;
+    c = __fadd2_rn(c, __fadd2_rn(err, e));
+  }
+  RK_DEV double value() const { return ((double)s.x + (double)c.x) + ((double)s.y + (double)c.y); }
+};
+#endif
+
 // ------------------------------------------------- compile-time trigonometry
 // cos and sin of 2*pi*m/R.  The angle is reduced exactly in integer arithmetic
 // to [0, pi/4] (octant symmetries), then evaluated with the Maclaurin series of

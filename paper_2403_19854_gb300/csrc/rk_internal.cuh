@@ -78,12 +78,18 @@ template <typename T>
 struct PointwiseArgs {
   T* D[10];
   int s;
-  const int* cidx;
-  const T* ctab;
+  const int* cidx;   // per node: -1 outside chi, 0 regular, 1 + row of ctab
+  const T* ctab;     // [n_irr][ctab_pitch<T>(s)]: b^x_p, b^y_p, b^z_p (s each), chi V, zero padding
   long long n_irr;
-  T breg[31];
+  T breg[31];        // the 3s+1 values of a regular node
   long long nbox;
 };
+// Row pitch of the table of irregular nodes: 3s+1 values padded to whole 16-byte
+// vectors, so that a row is read with 16-byte loads.
+template <typename T>
+constexpr int ctab_pitch(int s) {
+  return (3 * s + 1 + (int)(16 / sizeof(T)) - 1) / (int)(16 / sizeof(T)) * (int)(16 / sizeof(T));
+}
 template <typename T>
 cudaError_t launch_pointwise_stiff(const PointwiseArgs<T>& a, cudaStream_t s);
 

@@ -517,13 +517,12 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_merge(const Pass
         out[r1 + xp] = acc[r].y;
       }
     if (a.cg_p) {
-      DotAcc<T> dot;
+      DotAccPair<T> dot;
       if (ok)
 #pragma unroll
         for (int r = 0; r < X::R; ++r) {
           const int xp = F::nat_pos(t, r);
-          dot.add(a.cg_p[r0 + xp], acc[r].x);
-          dot.add(a.cg_p[r1 + xp], acc[r].y);
+          dot.add(cmk(a.cg_p[r0 + xp], a.cg_p[r1 + xp]), acc[r]);
         }
       cg_pap_reduce<X::THREADS>(dot.value(), a);
     }
@@ -552,16 +551,6 @@ struct ZArgs {
   const cpx<T>* tw;      // z-axis twiddles
   int nx, ny, nz;
   long long nbox;
-  // Z_STIFF with compressed coefficients (cidx != nullptr): per node -1 (outside
-  // chi), 0 (regular: the support lies in chi and V is the interior V, so b equals
-  // the interior values breg), or 1 + row of ctab.  ctab is [3s+1][n_irr]:
-  // b^x_p, b^y_p, b^z_p (s each) and chi V of the irregular nodes; breg the same
-  // 3s+1 values of a regular node.  With cidx == nullptr the full fields b and
-  // wfield are read instead.
-  const int* cidx;
-  const T* ctab;
-  long long n_irr;
-  T breg[3 * 10 + 1];
 };
 
 template <typename T, int N, int L, int MODE>
@@ -571,7 +560,7 @@ struct ZPass {
   static constexpr int P = F::P, R = F::R;
   static constexpr int THREADS = L * P;
   static constexpr size_t SMEM_BUF = sizeof(cpx<T>) * (size_t)N * L;
-  static constexpr size_t SMEM = SMEM_BUF * (MODE == Z_STIFF ? 4 : 1) + (MODE == Z_STIFF ? 256 : 0);
+  static constexpr size_t SMEM = SMEM_BUF * (MODE == Z_STIFF ? 4 : 1);
 };
 
 template <typename T, int N, int L, int MODE>
@@ -591,36 +580,6 @@ __global__ void __launch_bounds__(ZPass<T, N, L, MODE>::THREADS) k_z_fused(const
   auto A = [&](int k, int r) -> cpx<T>& { return Acc[((size_t)k * N + F::nat_pos(t, r)) * L + l]; };
   auto coef_pair = [&](int which, int p, long long off) -> cpx<T> {
     return ok ? S::load(a.b + ((long long)which * a.s + p) * a.nbox, off) : cmk((T)0, (T)0);
-  };
-  // compressed coefficients: class bits (2 per node: 0 outside, 1 regular,
-  // 2 irregular) of this thread's nodes, and the regular values in shared memory
-  unsigned cls[(Z::R + 7) / 8] = {};  // 4 bits per register: 2 per node of the pair
-  T* breg_s = reinterpret_cast<T*>(sm + (size_t)4 * N * L);
-  if (MODE == Z_STIFF && a.cidx) {
-    for (int j = threadIdx.x; j < 3 * a.s + 1; j += blockDim.x) breg_s[j] = a.breg[j];
-#pragma unroll
-    for (int r = 0; r < Z::R; ++r) {
-      int2 ci = make_int2(-1, -1);
-      if (ok) ci = *reinterpret_cast<const int2*>(a.cidx + base + F::nat_pos(t, r) * zs);
-      const unsigned c0 = ci.x < 0 ? 0u : (ci.x == 0 ? 1u : 2u);
-      const unsigned c1 = ci.y < 0 ? 0u : (ci.y == 0 ? 1u : 2u);
-      cls[r / 8] |= (c0 | (c1 << 2)) << (4 * (r % 8));
-    }
-  }
-  // coefficient j (b^k_p at j = k s + p, chi V at j = 3s) of the node pair at off
-  auto ccoef = [&](int r, long long off, int j) -> cpx<T> {
-    T out[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const unsigned k = (cls[r / 8] >> (4 * (r % 8) + 2 * c)) & 3u;
-      if (k == 0)
-        out[c] = (T)0;
-      else if (k == 1)
-        out[c] = breg_s[j];
-      else
-        out[c] = a.ctab[(long long)j * a.n_irr + (a.cidx[off + c] - 1)];
-    }
-    return cmk(out[0], out[1]);
   };
   cpx<T> v[Z::R], w[Z::R];
 
@@ -650,7 +609,7 @@ __global__ void __launch_bounds__(ZPass<T, N, L, MODE>::THREADS) k_z_fused(const
           if (MODE == Z_STIFF) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-              cpx<T> bk = a.cidx ? ccoef(r, off, k * a.s + p) : coef_pair(1 + k, p, off);
+              cpx<T> bk = coef_pair(1 + k, p, off);
               cpx<T>& Ak = A(k, r);
               Ak = pfma(bk, w[r], Ak);
             }
@@ -699,11 +658,11 @@ __global__ void __launch_bounds__(ZPass<T, N, L, MODE>::THREADS) k_z_fused(const
         const long long off = base + F::nat_pos(t, r) * zs;
         if (MODE == Z_STIFF) {
           // g_p = chi V sum_k b^k_p A^k   (Eq. 91: C^k_p = chi V b^k_p)
-          cpx<T> cv = a.cidx ? ccoef(r, off, 3 * a.s) : (ok ? S::load(a.wfield, off) : cmk((T)0, (T)0));
+          cpx<T> cv = ok ? S::load(a.wfield, off) : cmk((T)0, (T)0);
           cpx<T> s = cmk((T)0, (T)0);
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            cpx<T> bk = a.cidx ? ccoef(r, off, k * a.s + p) : coef_pair(1 + k, p, off);
+            cpx<T> bk = coef_pair(1 + k, p, off);
             cpx<T> Ak = A(k, r);
             s = pfma(bk, Ak, s);
           }

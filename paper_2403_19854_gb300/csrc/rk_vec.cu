@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(256) k_compact(const uint8_t* cls, const int* 
   }
   int pos = offsets[blockIdx.x] + sh[threadIdx.x] - c;
   const int ncoef = 3 * s + 1;
+  const int pitch = ctab_pitch<T>(s);
   for (int j = 0; j < PER; ++j) {
     const long long i = b0 + threadIdx.x * PER + j;
     if (i >= n) break;
@@ -152,8 +153,10 @@ __global__ void __launch_bounds__(256) k_compact(const uint8_t* cls, const int* 
       cidx[i] = 0;
     } else {
       cidx[i] = 1 + pos;
-      for (int q = 0; q < 3 * s; ++q) tab[(long long)q * n_irr + pos] = b[((long long)s + q) * n + i];
-      tab[(long long)(ncoef - 1) * n_irr + pos] = chiV[i];
+      T* row = tab + (long long)pos * pitch;
+      for (int q = 0; q < 3 * s; ++q) row[q] = b[((long long)s + q) * n + i];
+      row[ncoef - 1] = chiV[i];
+      for (int q = ncoef; q < pitch; ++q) row[q] = (T)0;
       ++pos;
     }
   }
@@ -184,9 +187,12 @@ cudaError_t launch_gather(double* out, const double* src, long long stride, long
 // Each thread owns VEC consecutive nodes (one 16-byte vector per field).
 template <typename T, int S>
 __global__ void __launch_bounds__(256) k_pointwise_stiff(const PointwiseArgs<T> a) {
-  constexpr int VEC = 16 / sizeof(T);
-  __shared__ T br[3 * S + 1];
-  for (int j = threadIdx.x; j < 3 * S + 1; j += blockDim.x) br[j] = a.breg[j];
+  constexpr int VEC = 16 / sizeof(T);        // nodes per thread and values per 16-byte vector
+  constexpr int NC = 3 * S + 1;              // b^x_p, b^y_p, b^z_p, chi V
+  constexpr int CP = ctab_pitch<T>(S);       // padded row of coefficients
+  using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  __shared__ __align__(16) T br[CP];
+  for (int j = threadIdx.x; j < CP; j += blockDim.x) br[j] = j < NC ? a.breg[j] : (T)0;
   __syncthreads();
   const long long nv = a.nbox / VEC;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
@@ -194,7 +200,7 @@ __global__ void __launch_bounds__(256) k_pointwise_stiff(const PointwiseArgs<T> 
     T d[S][VEC];
 #pragma unroll
     for (int q = 0; q < S; ++q) {
-      const float4 raw = *reinterpret_cast<const float4*>(a.D[q] + i0);
+      const V16 raw = *reinterpret_cast<const V16*>(a.D[q] + i0);
       memcpy(d[q], &raw, 16);
     }
     int ci[VEC];
@@ -213,37 +219,37 @@ __global__ void __launch_bounds__(256) k_pointwise_stiff(const PointwiseArgs<T> 
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
       const int c = ci[e];
-      T A[3] = {(T)0, (T)0, (T)0};
-      T cv = (T)0;
-      if (c == 0) {
+      // the node's coefficients: shared interior values or its row of the table
+      // (16-byte loads); the arithmetic below is the same for both
+      T co[CP];
+      if (c > 0) {
+        const V16* src = reinterpret_cast<const V16*>(a.ctab + (long long)(c - 1) * CP);
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-          for (int q = 0; q < S; ++q) A[k] += br[k * S + q] * d[q][e];
-        cv = br[3 * S];
-#pragma unroll
-        for (int p = 0; p < S; ++p) g[p][e] = cv * (br[p] * A[0] + br[S + p] * A[1] + br[2 * S + p] * A[2]);
-      } else if (c > 0) {
-        const T* row = a.ctab + (c - 1);
-        const long long ld = a.n_irr;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-          for (int q = 0; q < S; ++q) A[k] += row[(k * S + q) * ld] * d[q][e];
-        cv = row[3 * S * ld];
-#pragma unroll
-        for (int p = 0; p < S; ++p)
-          g[p][e] = cv * (row[p * ld] * A[0] + row[(S + p) * ld] * A[1] + row[(2 * S + p) * ld] * A[2]);
+        for (int k = 0; k < CP / VEC; ++k) {
+          const V16 raw = __ldg(src + k);
+          memcpy(co + k * VEC, &raw, 16);
+        }
       } else {
 #pragma unroll
-        for (int p = 0; p < S; ++p) g[p][e] = (T)0;
+        for (int k = 0; k < CP / VEC; ++k) {
+          const V16 raw = reinterpret_cast<const V16*>(br)[k];
+          memcpy(co + k * VEC, &raw, 16);
+        }
       }
+      T A[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int q = 0; q < S; ++q) A[k] += co[k * S + q] * d[q][e];
+      const T cv = c >= 0 ? co[3 * S] : (T)0;  // chi V; 0 outside chi
+#pragma unroll
+      for (int p = 0; p < S; ++p) g[p][e] = cv * (co[p] * A[0] + co[S + p] * A[1] + co[2 * S + p] * A[2]);
     }
 #pragma unroll
     for (int p = 0; p < S; ++p) {
-      float4 raw;
+      V16 raw;
       memcpy(&raw, g[p], 16);
-      *reinterpret_cast<float4*>(a.D[p] + i0) = raw;
+      *reinterpret_cast<V16*>(a.D[p] + i0) = raw;
     }
   }
 }
@@ -360,7 +366,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr_fused(T* __restrict__ x, 
                                                             unsigned* counter) {
   using V = Vec16<T>;
   const T al = (T)st->alpha;
-  DotAcc<T> acc;
+  DotAccPair<T> acc;
   const long long nv = n / V::N;
   for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < nv; i += (long long)kRedBlocks * kRedThreads) {
     V xv = reinterpret_cast<V*>(x)[i];
@@ -371,7 +377,11 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr_fused(T* __restrict__ x, 
     for (int e = 0; e < V::N; ++e) {
       xv.v[e] += al * pv.v[e];
       rv.v[e] -= al * av.v[e];
-      acc.add(rv.v[e], rv.v[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < V::N; e += 2) {
+      const cpx<T> rr = cmk(rv.v[e], rv.v[e + 1]);
+      acc.add(rr, rr);
     }
     reinterpret_cast<V*>(x)[i] = xv;
     reinterpret_cast<V*>(r)[i] = rv;
@@ -382,7 +392,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr_fused(T* __restrict__ x, 
     x[i] += al * p[i];
     const T ri = r[i] - al * Ap[i];
     r[i] = ri;
-    acc.add(ri, ri);
+    acc.add(cmk(ri, (T)0), cmk(ri, (T)0));
   }
   const double bs = block_sum(acc.value());
   __shared__ bool last;
