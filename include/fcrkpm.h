@@ -72,6 +72,13 @@ typedef struct rk_grid {
 
 typedef struct rk_handle rk_handle;
 
+/* Preconditioner of the CG solve.  The paper's Alg. 5 runs plain CG; the spectral
+ * preconditioner is an addition of this library (see rk_apply_precond). */
+typedef enum rk_precond {
+  RK_PRECOND_NONE = 0,
+  RK_PRECOND_SPECTRAL = 1
+} rk_precond;
+
 typedef struct rk_solve_opts {
   double tol;         /* stop when ||F - A d||_2 / ||F||_2 <= tol, FP64 residual (default 1e-10) */
   int32_t max_iter;   /* cap on CG iterations, all refinement steps together (default 200000) */
@@ -85,6 +92,9 @@ typedef struct rk_solve_opts {
                          when the FP32 iterations stop reducing the FP64 residual (three
                          replacements in a row without halving it, or max_outer reached);
                          0 returns RK_ERR_NOT_CONVERGED there instead */
+  int32_t precond;    /* rk_precond: RK_PRECOND_NONE (default, the plain CG of Alg. 5) or
+                         RK_PRECOND_SPECTRAL (see rk_apply_precond) */
+  int32_t reserved;   /* 0 */
 } rk_solve_opts;
 
 typedef struct rk_solve_info {
@@ -142,6 +152,22 @@ rk_status rk_singular_nodes(const rk_handle* h, int64_t* count, int64_t* first);
  *   dtype  RK_F64: double arrays, FP64 path;  RK_F32: float arrays, FP32 path
  */
 rk_status rk_apply_K(rk_handle* h, const void* d, void* f, int32_t dtype, void* stream);
+
+/*
+ * rk_apply_precond -- z = M^{-1} r, the spectral preconditioner of
+ * RK_PRECOND_SPECTRAL (no counterpart in the paper, whose Alg. 5 runs plain CG):
+ *   z = chi_Omega o F^{-1}[ F(r) / (lam + shift) ]
+ * with F the 3D DFT of the periodic box (Eq. 30), lam(theta) = V sum_k |D^_k(theta)|^2
+ * the eigenvalues of K on a box of regular nodes (whole support in chi, interior V;
+ * D^_k = sum_p b^k_p prod_axis T^_{alpha(p)}, the DFTs of the separable kernel
+ * tables of Eq. 77-79 and the interior correction coefficients of Eq. 83-85), and
+ * shift = 1e-3 lam(2 pi / n_x, 0, 0), which keeps the constant mode invertible.  M^{-1}
+ * is symmetric positive definite on chi_Omega, as PCG requires.
+ * r, z: box arrays (x fastest) of dtype RK_F64 or RK_F32, host or device.
+ * Errors: RK_ERR_UNSUPPORTED when the domain has no regular node or a box side
+ * exceeds 256.
+ */
+rk_status rk_apply_precond(rk_handle* h, const void* r, void* z, int32_t dtype, void* stream);
 
 /* rk_rhs -- Alg. 4 with the reflected kernel of Eq. 60/92:
  * f^r = chi o F^-1[ sum_p F(chi o V o b^0_p o r) o F(Hbar^a_p) ].  r, fr: double[nbox]. */
@@ -222,7 +248,8 @@ enum {
   RK_PROF_MOMENT_SOLVE = 8,  /* per-node M^{-1} of Alg. 1 */
   RK_PROF_CG_VECTOR = 9,     /* CG dot products and vector updates (per iteration) */
   RK_PROF_Z_MERGE = 10,      /* z pass, reflected chain */
-  RK_PROF_CLASSES = 11
+  RK_PROF_PRECOND = 11,      /* spectral preconditioner (five passes) */
+  RK_PROF_CLASSES = 12
 };
 
 /* Total number of kernels this library has launched in the process. */

@@ -145,7 +145,7 @@ struct rk_handle {
   float* ws32 = nullptr;
   // solver vectors (allocated on first solve)
   double* sv64 = nullptr;  // x, r, p, Ap, F, d0, t0, t1
-  float* sv32 = nullptr;   // x, r, p, Ap
+  float* sv32 = nullptr;   // x, r, p, Ap, z
   double* partials = nullptr;
   double* xpartials = nullptr;  // one partial p.Ap per block of the x MERGE pass
   unsigned* counters2 = nullptr;  // [0]: x MERGE blocks done, [1]: update blocks done
@@ -156,6 +156,17 @@ struct rk_handle {
   std::vector<CUtensorMap> tmaps32[2], tmaps64[2];
   int* err_host = nullptr;   // mapped pinned word: a bounded device wait gave up
   int* err_dev = nullptr;    // its device address
+  // spectral preconditioner: half spectra (per handle, rows of nxp complex); the
+  // per-axis symbol factors, the symbol parameters and the multiplier tables live
+  // in the set-up handle and are shared with its clones
+  cpx<float>* spec32 = nullptr;
+  cpx<double>* spec64 = nullptr;
+  int nxp = 0;
+  double* symc64[3] = {nullptr, nullptr, nullptr};
+  bool pc_ready = false;
+  SymbolArgs<double> sym64;
+  float* mult32 = nullptr;   // z SYM multiplier tables (owned by the set-up handle)
+  double* mult64 = nullptr;
   // staging of host arrays
   double* stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   unsigned long long* counters = nullptr;  // singular count, first singular
@@ -253,7 +264,7 @@ constexpr int prof_cls(int c) {
 
 const char* const kProfNames[RK_PROF_CLASSES] = {"x_split", "y_split", "z_split", "stiff_pointwise", "z_eval_u",
                                                  "z_transpose_u", "y_merge", "x_merge", "moment_solve", "cg_vector",
-                                                 "z_merge"};
+                                                 "z_merge", "precond"};
 
 template <typename T>
 const T* coef_of(const rk_handle* h, int axis);
@@ -752,8 +763,8 @@ rk_status check_device_flag(rk_handle* h) {
 
 // ------------------------------------------------------------------ solver
 rk_status ensure_solver(rk_handle* h) {
-  if (!h->sv64) RK_TRY(h->alloc(&h->sv64, (size_t)8 * h->nbox));
-  if (!h->sv32) RK_TRY(h->alloc(&h->sv32, (size_t)4 * h->nbox));
+  if (!h->sv64) RK_TRY(h->alloc(&h->sv64, (size_t)9 * h->nbox));
+  if (!h->sv32) RK_TRY(h->alloc(&h->sv32, (size_t)5 * h->nbox));
   if (!h->partials) RK_TRY(h->alloc(&h->partials, (size_t)kRedBlocks));
   if (!h->xpartials) RK_TRY(h->alloc(&h->xpartials, (size_t)((long long)h->n[1] * h->n[2] / 2 + 1)));
   if (!h->counters2) {
@@ -764,7 +775,7 @@ rk_status ensure_solver(rk_handle* h) {
   if (!h->cg) RK_TRY(h->alloc(&h->cg, (size_t)1));
   if (!h->hscal) {
     void* p = nullptr;
-    RK_CK(cudaMallocHost(&p, 8 * sizeof(double)));
+    RK_CK(cudaMallocHost(&p, 16 * sizeof(double)));  // a CGState or a scalar
     h->hscal = (double*)p;
   }
   return RK_OK;
@@ -786,15 +797,157 @@ rk_status norm2(rk_handle* h, const double* v, double* out, cudaStream_t s) {
   return RK_OK;
 }
 
+// ----------------------------------------------------- spectral preconditioner
+template <typename T>
+T*& mult_of(rk_handle* h);
+template <>
+double*& mult_of<double>(rk_handle* h) { return h->mult64; }
+template <>
+float*& mult_of<float>(rk_handle* h) { return h->mult32; }
+template <typename T>
+cpx<T>*& spec_of(rk_handle* h);
+template <>
+cpx<double>*& spec_of<double>(rk_handle* h) { return h->spec64; }
+template <>
+cpx<float>*& spec_of<float>(rk_handle* h) { return h->spec32; }
+
+// Symbol of the operator at regular nodes (see rk_precond.cuh): per-axis real
+// factors c_m(k) of the table spectra T^_m (m <= degree; i per odd m applied via
+// imag/sgn), the interior b^k_p and V, the shift 1e-3 lam(2 pi / n_x, 0, 0) and
+// the 1/(n_x n_y n_z) of the unnormalised transforms.
+rk_status ensure_precond(rk_handle* h) {
+  if (h->pc_ready) return RK_OK;
+  if (h->parent) {
+    // a clone shares the parent's symbol (set up once, on the first use by either)
+    rk_handle* par = const_cast<rk_handle*>(h->parent);
+    RK_TRY(ensure_precond(par));
+  } else {
+    if (!(h->breg64[3 * h->s] > 0.0))
+      return fail(RK_ERR_UNSUPPORTED, "spectral preconditioner: the domain has no regular node");
+    for (int k = 0; k < 3; ++k)
+      if (h->n[k] > 256) return fail(RK_ERR_UNSUPPORTED, "spectral preconditioner: box side above 256");
+    int alpha[10][3];
+    basis_exponents(h->degree, alpha);
+    std::vector<double> c[3];
+    for (int ax = 0; ax < 3; ++ax) {
+      const int n = h->n[ax];
+      std::vector<double> coef;
+      std::vector<cpx<double>> tw;
+      axis_tables(n, h->a_tilde, h->reach, 2 * h->degree, coef, tw);
+      c[ax].assign((size_t)(h->degree + 1) * n, 0.0);
+      for (int m = 0; m <= h->degree; ++m)
+        for (int k = 0; k < n; ++k) c[ax][(size_t)m * n + k] = (double)n * coef[(size_t)m * n + k];
+      RK_TRY(h->alloc(&h->symc64[ax], c[ax].size()));
+      RK_CK(cudaMemcpy(h->symc64[ax], c[ax].data(), c[ax].size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    SymbolArgs<double> y;
+    memset(&y, 0, sizeof(y));
+    for (int k = 0; k < 3; ++k) y.n[k] = h->n[k];
+    y.s = h->s;
+    for (int p = 0; p < h->s; ++p) {
+      int odd = 0;
+      for (int k = 0; k < 3; ++k) {
+        y.alpha[p][k] = alpha[p][k];
+        odd += alpha[p][k] % 2;
+      }
+      y.imag[p] = odd % 2;           // i^odd: 1, i, -1, -i
+      y.sgn[p] = (odd % 4 < 2) ? 1.0 : -1.0;
+      for (int k = 0; k < 3; ++k) y.b[k][p] = h->breg64[k * h->s + p];
+    }
+    y.vreg = h->breg64[3 * h->s];
+    // lam at the first x frequency, in FP64 on the host
+    double R[3] = {0, 0, 0}, I[3] = {0, 0, 0};
+    for (int p = 0; p < h->s; ++p) {
+      const double f = y.sgn[p] * c[0][(size_t)y.alpha[p][0] * h->n[0] + 1] * c[1][(size_t)y.alpha[p][1] * h->n[1]] *
+                       c[2][(size_t)y.alpha[p][2] * h->n[2]];
+      for (int k = 0; k < 3; ++k) (y.imag[p] ? I[k] : R[k]) += y.b[k][p] * f;
+    }
+    double lam1 = 0.0;
+    for (int k = 0; k < 3; ++k) lam1 += R[k] * R[k] + I[k] * I[k];
+    lam1 *= y.vreg;
+    if (!(lam1 > 0.0)) return fail(RK_ERR_UNSUPPORTED, "spectral preconditioner: degenerate symbol");
+    y.shift = 1e-3 * lam1;
+    y.scale = 1.0 / ((double)h->n[0] * h->n[1] * h->n[2]);
+    y.cx = h->symc64[0];
+    y.cy = h->symc64[1];
+    y.cz = h->symc64[2];
+    h->sym64 = y;
+  }
+  h->nxp = (h->n[0] / 2 + 1 + 1) / 2 * 2;
+  h->pc_ready = true;
+  return RK_OK;
+}
+
+// z = M^{-1} r (rk_precond.cuh), five passes on stream s.  With fused CG state
+// (rz_mode >= 0) the last pass also forms r.z and beta.
+template <typename T>
+rk_status apply_precond(rk_handle* h, const T* r, T* z, cudaStream_t s, int rz_mode) {
+  RK_TRY(ensure_precond(h));
+  cpx<T>*& S = spec_of<T>(h);
+  if (!S) RK_TRY(h->alloc(&S, (size_t)h->nxp * h->n[1] * h->n[2]));
+  ProfScope ps(h, prof_cls<T>(RK_PROF_PRECOND), s);
+  PxArgs<T> px;
+  memset(&px, 0, sizeof(px));
+  px.in = r;
+  px.S = S;
+  px.nxp = h->nxp;
+  px.tw = tw_of<T>(h, 0);
+  px.nx = h->n[0];
+  px.ny = h->n[1];
+  px.nz = h->n[2];
+  cudaError_t e = launch_px<T>(0, h->n[0], px, s);
+  PfftArgs<T> py;
+  memset(&py, 0, sizeof(py));
+  py.S = S;
+  py.ncols = h->nxp;
+  py.line_stride = h->nxp;
+  py.other_stride = (long long)h->nxp * h->n[1];
+  py.nother = h->n[2];
+  py.tw = tw_of<T>(h, 1);
+  if (e == cudaSuccess) e = launch_pfft<T>(PF_FWD, h->n[1], py, s);
+  PfftArgs<T> pz = py;
+  pz.line_stride = (long long)h->nxp * h->n[1];
+  pz.other_stride = h->nxp;
+  pz.nother = h->n[1];
+  pz.tw = tw_of<T>(h, 2);
+  rk_handle* owner = h->parent ? const_cast<rk_handle*>(h->parent) : h;
+  T*& mult = mult_of<T>(owner);
+  if (!mult) {
+    RK_TRY(owner->alloc(&mult, (size_t)owner->nxp * h->n[1] * h->n[2]));
+    RK_CK(launch_symbol_table<T>(owner->sym64, mult, owner->nxp, h->n[1], h->n[2], s));
+  }
+  pz.mult = mult;
+  if (e == cudaSuccess) e = launch_pfft<T>(PF_SYM, h->n[2], pz, s);
+  if (e == cudaSuccess) e = launch_pfft<T>(PF_INV, h->n[1], py, s);
+  px.in = nullptr;
+  px.out = z;
+  px.out_mask = h->chi_omega;
+  if (rz_mode >= 0) {
+    px.cg_r = r;
+    px.cg = h->cg;
+    px.partials = h->xpartials;
+    px.counter = h->counters2;
+    px.rz_mode = rz_mode;
+  }
+  if (e == cudaSuccess) e = launch_px<T>(1, h->n[0], px, s);
+  return e == cudaSuccess ? RK_OK : cuda_fail(e, "preconditioner");
+}
+
 // CG on the masked operator A v = chi_Omega o K(chi_Omega o v) in precision T.
 // On entry x holds the initial iterate and r = b - A x.  Stops when r.r <= rr_target.
+// With pcg, z = M^{-1} r is formed after every update (z holds it) and the search
+// direction follows z (PCG); else z is unused.
 template <typename T>
-rk_status cg_run(rk_handle* h, T* x, T* r, T* p, T* Ap, double rr_target, int max_iter, int check_every,
-                 cudaStream_t s, int* iters, double* rr_final, int* matvecs) {
+rk_status cg_run(rk_handle* h, T* x, T* r, T* p, T* Ap, T* z, bool pcg, double rr_target, int max_iter,
+                 int check_every, cudaStream_t s, int* iters, double* rr_final, int* matvecs) {
   const long long n = h->nbox;
-  RK_CK(launch_copy<T>(p, r, n, s));
+  if (pcg)
+    RK_CK(launch_fill<T>(p, (T)0, n, s));
+  else
+    RK_CK(launch_copy<T>(p, r, n, s));
   RK_CK(launch_dot<T, T>(r, r, n, h->partials, h->dscal, s));
-  RK_CK(launch_cg_init(h->partials, h->cg, s));
+  RK_CK(launch_cg_init(h->partials, h->cg, pcg ? 1 : 0, s));
+  if (pcg) RK_TRY(apply_precond<T>(h, r, z, s, 2));
   int it = 0;
   double rr = 0.0;
   for (;;) {
@@ -808,20 +961,21 @@ rk_status cg_run(rk_handle* h, T* x, T* r, T* p, T* Ap, double rr_target, int ma
       if (st.flag) {
         *iters = it;
         *rr_final = rr;
-        return fail(RK_ERR_BREAKDOWN, "CG breakdown (p^T A p <= 0 or not finite)");
+        return fail(RK_ERR_BREAKDOWN, "CG breakdown (p^T A p <= 0, r^T z <= 0 or not finite)");
       }
       if (!(rr > rr_target) || it >= max_iter) break;
     }
     // one iteration: p = r + beta p (x pass prologue), Ap (p is zero off chi_Omega,
     // so only the output mask applies), p.Ap -> alpha (x pass epilogue), then
     // x += alpha p, r -= alpha Ap, r.r -> beta
-    const CGFuse<T> fz{p, r};
+    const CGFuse<T> fz{p, pcg ? z : r};
     RK_TRY(op_K<T>(h, p, Ap, nullptr, h->chi_omega, s, &fz));
     ++*matvecs;
     {
       ProfScope ps(h, prof_cls<T>(RK_PROF_CG_VECTOR), s);
       RK_CK(launch_cg_xr_fused<T>(x, r, p, Ap, h->cg, n, h->partials, h->counters2 + 1, s));
     }
+    if (pcg) RK_TRY(apply_precond<T>(h, r, z, s, 0));
     ++it;
   }
   *iters = it;
@@ -854,6 +1008,7 @@ struct MixedJob {
   bool done = false;
   bool use_graph = false;
   bool fp64_tail = false;  // the mixed iterations stalled: finish in FP64
+  bool pcg = false;        // preconditioned (opts.precond)
 };
 
 // r64 = F - A64 x (FP64 operator), rn = |r64|
@@ -869,11 +1024,16 @@ rk_status true_residual64(rk_handle* h, const double* F, const double* x, rk_sol
 rk_status mixed_start(MixedJob& j) {
   rk_handle* h = j.h;
   const long long n = h->nbox;
+  j.pcg = j.o.precond != 0;
   RK_CK(launch_to_f32(h->v32(1), h->v64(1), 1.0, n, j.s));
   RK_CK(launch_fill<float>(h->v32(0), 0.0f, n, j.s));
-  RK_CK(launch_copy<float>(h->v32(2), h->v32(1), n, j.s));
+  if (j.pcg)
+    RK_CK(launch_fill<float>(h->v32(2), 0.0f, n, j.s));
+  else
+    RK_CK(launch_copy<float>(h->v32(2), h->v32(1), n, j.s));
   RK_CK(launch_dot<float, float>(h->v32(1), h->v32(1), n, h->partials, h->dscal, j.s));
-  RK_CK(launch_cg_init(h->partials, h->cg, j.s));
+  RK_CK(launch_cg_init(h->partials, h->cg, j.pcg ? 1 : 0, j.s));
+  if (j.pcg) RK_TRY(apply_precond<float>(h, h->v32(1), h->v32(4), j.s, 2));
   j.rmax = j.best = j.rn;
   j.done = j.rn <= j.target;
   return RK_OK;
@@ -886,10 +1046,13 @@ rk_status mixed_iteration(MixedJob& j) {
   float* r32 = h->v32(1);
   float* p32 = h->v32(2);
   float* Ap32 = h->v32(3);
-  const CGFuse<float> fz{p32, r32};
+  const CGFuse<float> fz{p32, j.pcg ? h->v32(4) : r32};
   RK_TRY(op_K<float>(h, p32, Ap32, nullptr, h->chi_omega, j.s, &fz));
-  ProfScope ps(h, prof_cls<float>(RK_PROF_CG_VECTOR), j.s);
-  RK_CK(launch_cg_xr_fused<float>(x32, r32, p32, Ap32, h->cg, h->nbox, h->partials, h->counters2 + 1, j.s));
+  {
+    ProfScope ps(h, prof_cls<float>(RK_PROF_CG_VECTOR), j.s);
+    RK_CK(launch_cg_xr_fused<float>(x32, r32, p32, Ap32, h->cg, h->nbox, h->partials, h->counters2 + 1, j.s));
+  }
+  if (j.pcg) RK_TRY(apply_precond<float>(h, r32, h->v32(4), j.s, 0));
   return RK_OK;
 }
 
@@ -973,9 +1136,15 @@ rk_status mixed_check(MixedJob& j) {
   RK_CK(launch_to_f32(h->v32(1), h->v64(1), 1.0, n, j.s));
   RK_CK(launch_dot<float, float>(h->v32(1), h->v32(1), n, h->partials, h->dscal, j.s));
   if (cs.flag) {  // restart the direction after a breakdown
-    RK_CK(launch_copy<float>(h->v32(2), h->v32(1), n, j.s));
-    RK_CK(launch_cg_init(h->partials, h->cg, j.s));
+    if (j.pcg)
+      RK_CK(launch_fill<float>(h->v32(2), 0.0f, n, j.s));
+    else
+      RK_CK(launch_copy<float>(h->v32(2), h->v32(1), n, j.s));
+    RK_CK(launch_cg_init(h->partials, h->cg, j.pcg ? 1 : 0, j.s));
+    if (j.pcg) RK_TRY(apply_precond<float>(h, h->v32(1), h->v32(4), j.s, 2));
   } else {
+    // only r is replaced: z, r.z and beta keep their recurrence values, so the next
+    // direction stays conjugate; the next preconditioner application sees the true r
     RK_CK(launch_cg_set_rr(h->partials, h->cg, j.s));
   }
   j.rmax = j.rn;
@@ -990,8 +1159,8 @@ rk_status fp64_cg(rk_handle* h, const double* F, double* x, double target, const
   for (int restart = 0; restart < 8 && *rn > target && *total < o.max_iter; ++restart) {
     int it = 0, mv = 0;
     double rr;
-    rk_status st = cg_run<double>(h, x, h->v64(1), h->v64(2), h->v64(3), target * target, o.max_iter - *total,
-                                  o.check_every, s, &it, &rr, &mv);
+    rk_status st = cg_run<double>(h, x, h->v64(1), h->v64(2), h->v64(3), h->v64(8), o.precond != 0, target * target,
+                                  o.max_iter - *total, o.check_every, s, &it, &rr, &mv);
     *total += it;
     info->fp64_iterations += it;
     info->matvec_f64 += mv;
@@ -1066,12 +1235,14 @@ void fill_defaults(rk_solve_opts* o) {
   o->check_every = 25;
   o->x0_given = 0;
   o->fp64_finish = 1;
+  o->precond = RK_PRECOND_NONE;
+  o->reserved = 0;
 }
 
 rk_status check_opts(const rk_solve_opts& o) {
   if (!(o.tol > 0.0) || o.max_iter < 1 || (o.precision != RK_PREC_FP64 && o.precision != RK_PREC_MIXED) ||
       !(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.max_outer < 1 || o.check_every < 1 ||
-      (o.fp64_finish != 0 && o.fp64_finish != 1))
+      (o.fp64_finish != 0 && o.fp64_finish != 1) || (o.precond != RK_PRECOND_NONE && o.precond != RK_PRECOND_SPECTRAL))
     return fail(RK_ERR_INVALID_ARG, "invalid solve options");
   return RK_OK;
 }
@@ -1543,6 +1714,8 @@ rk_status rk_clone(const rk_handle* parent, rk_handle** out) {
   h->chunk_len = 0;
   h->err_host = nullptr;
   h->err_dev = nullptr;
+  h->spec32 = nullptr;
+  h->spec64 = nullptr;
   for (int k = 0; k < 2; ++k) {
     h->tmaps32[k].clear();
     h->tmaps64[k].clear();
@@ -1682,6 +1855,24 @@ rk_status rk_apply_K(rk_handle* h, const void* d, void* f, int32_t dtype, void* 
     RK_CK(cudaStreamSynchronize(s));
     RK_TRY(check_device_flag(h));
   }
+  return RK_OK;
+}
+
+rk_status rk_apply_precond(rk_handle* h, const void* r, void* z, int32_t dtype, void* stream) {
+  if (!h || !r || !z) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  if (dtype != RK_F64 && dtype != RK_F32) return fail(RK_ERR_INVALID_ARG, "bad dtype");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * (dtype == RK_F64 ? 8 : 4);
+  RK_TRY(ensure_solver(h));
+  Staged sr, sz;
+  RK_TRY(stage_in(h, 0, r, bytes, s, &sr));
+  RK_TRY(stage_out_prepare(h, 1, z, bytes, &sz));
+  if (dtype == RK_F64)
+    RK_TRY(apply_precond<double>(h, (const double*)sr.dev, (double*)sz.dev, s, -1));
+  else
+    RK_TRY(apply_precond<float>(h, (const float*)sr.dev, (float*)sz.dev, s, -1));
+  RK_TRY(stage_out_finish(sz, s));
+  if (any_host({&sr, &sz})) RK_CK(cudaStreamSynchronize(s));
   return RK_OK;
 }
 

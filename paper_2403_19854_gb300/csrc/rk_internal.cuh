@@ -7,6 +7,7 @@
 #include <atomic>
 
 #include "rk_passes.cuh"
+#include "rk_precond.cuh"
 
 namespace rk {
 
@@ -100,20 +101,27 @@ constexpr int kRedThreads = 256;
 
 template <typename Ta, typename Tb>
 cudaError_t launch_dot(const Ta* a, const Tb* b, long long n, double* partials, double* out, cudaStream_t s);
-cudaError_t launch_cg_alpha(const double* partials, CGState* st, cudaStream_t s);
-template <typename T>
-cudaError_t launch_cg_xr(T* x, T* r, const T* p, const T* Ap, CGState* st, long long n, double* partials,
-                         cudaStream_t s);
-cudaError_t launch_cg_beta(const double* partials, CGState* st, cudaStream_t s);
-template <typename T>
-cudaError_t launch_cg_p(T* p, const T* r, const CGState* st, long long n, cudaStream_t s);
-cudaError_t launch_cg_init(const double* partials, CGState* st, cudaStream_t s);
-// rr = sum(partials), leaving beta and the search direction as they are
+// rr = sum(partials), alpha = beta = 0, flag cleared; pcg selects who forms r.z
+// (without preconditioner rz = rr)
+cudaError_t launch_cg_init(const double* partials, CGState* st, int pcg, cudaStream_t s);
+// rr = sum(partials) after a residual replacement, leaving beta and the search
+// direction as they are (rz too without preconditioner)
 cudaError_t launch_cg_set_rr(const double* partials, CGState* st, cudaStream_t s);
-// x += alpha p, r -= alpha Ap; the last block sets rr_new, beta = rr_new / rr, rr = rr_new
+// x += alpha p, r -= alpha Ap; the last block sets rr_new and rr, and without
+// preconditioner also beta = rr_new / rr and rz = rr_new
 template <typename T>
 cudaError_t launch_cg_xr_fused(T* x, T* r, const T* p, const T* Ap, CGState* st, long long n, double* partials,
                                unsigned* counter, cudaStream_t s);
+
+// spectral preconditioner passes (rk_precond.cuh): x R2C / C2R and the complex
+// y / z passes, dispatched by line length
+template <typename T>
+cudaError_t launch_px(int c2r, int n, const PxArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pfft(int mode, int n, const PfftArgs<T>& a, cudaStream_t s);
+// the multiplier table of the z SYM pass, computed in FP64
+template <typename T>
+cudaError_t launch_symbol_table(const SymbolArgs<double>& y, T* tab, int nxp, int ny, int nz, cudaStream_t s);
 
 // elementwise helpers (double unless noted)
 cudaError_t launch_dirichlet_d0(double* d0, const double* g, const uint8_t* chi_gamma, long long n, cudaStream_t s);

@@ -124,6 +124,56 @@ cudaError_t z_n(int mode, const ZArgs<T>& a, cudaStream_t s) {
   }
 }
 
+// spectral preconditioner passes (rk_precond.cuh)
+template <typename T, int N>
+cudaError_t px_n(int c2r, const PxArgs<T>& a, cudaStream_t s) {
+  constexpr int LX = Cfg<T>::XTHREADS / LineShape<N>::P;
+  using X = XPass<T, N, LX>;
+  const long long npairs = ((long long)a.ny * a.nz) / 2;
+  const unsigned nb = (unsigned)((npairs + LX - 1) / LX);
+  auto k = c2r ? k_px_c2r<T, N, LX> : k_px_r2c<T, N, LX>;
+  cudaError_t e = set_smem(k, X::SMEM);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  k<<<nb, X::THREADS, X::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int N, int MODE>
+cudaError_t pfft_n_mode(const PfftArgs<T>& a, cudaStream_t s) {
+  constexpr int L = Cfg<T>::L;
+  using S = Strided<T, N, L>;
+  auto kernel = k_pfft<T, N, L, MODE>;
+  static int resident = 0;
+  static int sms = 0;
+  if (!resident) {
+    cudaError_t e = set_smem(kernel, S::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nb = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, S::THREADS, S::SMEM)) != cudaSuccess) return e;
+    sms = nsm;
+    resident = nb > 0 ? nb : 1;
+  }
+  const int nbx = (a.ncols + L - 1) / L;
+  const long long ntiles = (long long)nbx * a.nother;
+  const long long cap = (long long)resident * sms;
+  count_launch();
+  kernel<<<(unsigned)(ntiles < cap ? ntiles : cap), S::THREADS, S::SMEM, s>>>(a, nbx, ntiles);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t pfft_n(int mode, const PfftArgs<T>& a, cudaStream_t s) {
+  switch (mode) {
+    case PF_FWD: return pfft_n_mode<T, N, PF_FWD>(a, s);
+    case PF_SYM: return pfft_n_mode<T, N, PF_SYM>(a, s);
+    case PF_INV: return pfft_n_mode<T, N, PF_INV>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // One translation unit per line length instantiates split_n, merge_n and z_n for
 // both precisions (rk_len_<N>.cu); rk_dispatch.cu selects them at run time.
 #define RK_FOR_EACH_LENGTH(X) X(8) X(16) X(32) X(36) X(48) X(64) X(72) X(96) X(100) X(128) X(144) X(162) X(256)
@@ -134,7 +184,11 @@ cudaError_t z_n(int mode, const ZArgs<T>& a, cudaStream_t s) {
   extern template cudaError_t merge_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*);   \
   extern template cudaError_t merge_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*); \
   extern template cudaError_t z_n<float, N>(int, const ZArgs<float>&, cudaStream_t);          \
-  extern template cudaError_t z_n<double, N>(int, const ZArgs<double>&, cudaStream_t);
+  extern template cudaError_t z_n<double, N>(int, const ZArgs<double>&, cudaStream_t);        \
+  extern template cudaError_t px_n<float, N>(int, const PxArgs<float>&, cudaStream_t);        \
+  extern template cudaError_t px_n<double, N>(int, const PxArgs<double>&, cudaStream_t);      \
+  extern template cudaError_t pfft_n<float, N>(int, const PfftArgs<float>&, cudaStream_t);    \
+  extern template cudaError_t pfft_n<double, N>(int, const PfftArgs<double>&, cudaStream_t);
 
 #define RK_INSTANTIATE_LENGTH(N)                                                       \
   template cudaError_t split_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*);   \
@@ -142,6 +196,10 @@ cudaError_t z_n(int mode, const ZArgs<T>& a, cudaStream_t s) {
   template cudaError_t merge_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*);   \
   template cudaError_t merge_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*); \
   template cudaError_t z_n<float, N>(int, const ZArgs<float>&, cudaStream_t);          \
-  template cudaError_t z_n<double, N>(int, const ZArgs<double>&, cudaStream_t);
+  template cudaError_t z_n<double, N>(int, const ZArgs<double>&, cudaStream_t);        \
+  template cudaError_t px_n<float, N>(int, const PxArgs<float>&, cudaStream_t);        \
+  template cudaError_t px_n<double, N>(int, const PxArgs<double>&, cudaStream_t);      \
+  template cudaError_t pfft_n<float, N>(int, const PfftArgs<float>&, cudaStream_t);    \
+  template cudaError_t pfft_n<double, N>(int, const PfftArgs<double>&, cudaStream_t);
 
 }  // namespace rk

@@ -42,14 +42,17 @@ RK_HD cpx<T> spec_mul(cpx<T> v, const T* __restrict__ coef, int N, int m, int k,
 
 // Scalars of the conjugate-gradient recurrence, kept in device memory.
 struct CGState {
-  double rr;      // r.r of the current iterate
+  double rr;      // r.r of the current iterate (convergence)
   double pAp;
-  double alpha;
-  double beta;
+  double alpha;   // rz / pAp
+  double beta;    // rz_new / rz_prev
   double rr_new;
-  int flag;       // 1: breakdown (p^T A p <= 0 or not finite)
-  int pad;
+  double rz;      // r.z (z = M^{-1} r; z = r without preconditioner, then rz = rr)
+  double rz_prev;
+  int flag;       // 1: breakdown (p^T A p <= 0, r.z <= 0 or not finite)
+  int pcg;        // 1: z = M^{-1} r is formed by the preconditioner, which sets rz and beta
 };
+static_assert(sizeof(CGState) <= 16 * sizeof(double), "CGState must fit the pinned host slot");
 
 template <typename T>
 struct PassArgs {
@@ -386,9 +389,9 @@ __device__ __forceinline__ void cg_pap_reduce(double v, const PassArgs<T>& a) {
     CGState* st = a.cg;
     st->pAp = pap;
     double al = 0.0;
-    if (st->rr > 0.0) {
+    if (st->rz > 0.0) {
       if (pap > 0.0 && isfinite(pap))
-        al = st->rr / pap;
+        al = st->rz / pap;
       else
         st->flag = 1;
     }

@@ -270,6 +270,27 @@ cudaError_t launch_pointwise_stiff(const PointwiseArgs<T>& a, cudaStream_t s) {
 template cudaError_t launch_pointwise_stiff<float>(const PointwiseArgs<float>&, cudaStream_t);
 template cudaError_t launch_pointwise_stiff<double>(const PointwiseArgs<double>&, cudaStream_t);
 
+// ------------------------------------------------ preconditioner symbol
+// tab[kz][ky][kx] = scale / lam~(kx, ky, kz) for kx < nxp (padding columns use kx = 0)
+template <typename T>
+__global__ void k_symbol_table(const SymbolArgs<double> y, T* tab, int nxp, int ny, int nz) {
+  const long long n = (long long)nxp * ny * nz;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % nxp), ky = (int)((i / nxp) % ny), kz = (int)(i / ((long long)nxp * ny));
+    tab[i] = (T)(y.scale / symbol_value(y, kx < y.n[0] ? kx : 0, ky, kz));
+  }
+}
+template <typename T>
+cudaError_t launch_symbol_table(const SymbolArgs<double>& y, T* tab, int nxp, int ny, int nz, cudaStream_t s) {
+  const long long n = (long long)nxp * ny * nz;
+  const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
+  count_launch();
+  k_symbol_table<T><<<grid, 256, 0, s>>>(y, tab, nxp, ny, nz);
+  return cudaGetLastError();
+}
+template cudaError_t launch_symbol_table<float>(const SymbolArgs<double>&, float*, int, int, int, cudaStream_t);
+template cudaError_t launch_symbol_table<double>(const SymbolArgs<double>&, double*, int, int, int, cudaStream_t);
+
 // ----------------------------------------------------------- reductions
 // Fixed grid and fixed combination order: results are bit-reproducible.
 __device__ __forceinline__ double warp_sum(double v) {
@@ -326,25 +347,31 @@ cudaError_t launch_dot(const Ta* a, const Tb* b, long long n, double* partials, 
 template cudaError_t launch_dot<double, double>(const double*, const double*, long long, double*, double*, cudaStream_t);
 template cudaError_t launch_dot<float, float>(const float*, const float*, long long, double*, double*, cudaStream_t);
 
-// rr = sum(partials); alpha = beta = 0
-__global__ void k_cg_init(const double* part, CGState* st) {
+// rr = sum(partials); alpha = beta = 0; without preconditioner rz = rr
+__global__ void k_cg_init(const double* part, CGState* st, int pcg) {
   const double v = reduce_partials(part);
   if (threadIdx.x == 0) {
     st->rr = v;
     st->alpha = 0.0;
     st->beta = 0.0;
     st->flag = 0;
+    st->pcg = pcg;
+    if (!pcg) st->rz = st->rz_prev = v;
   }
 }
-cudaError_t launch_cg_init(const double* partials, CGState* st, cudaStream_t s) {
+cudaError_t launch_cg_init(const double* partials, CGState* st, int pcg, cudaStream_t s) {
   count_launch();
-  k_cg_init<<<1, kRedThreads, 0, s>>>(partials, st);
+  k_cg_init<<<1, kRedThreads, 0, s>>>(partials, st, pcg);
   return cudaGetLastError();
 }
 
+// rr = sum(partials) after a residual replacement (rz too without preconditioner)
 __global__ void k_cg_set_rr(const double* part, CGState* st) {
   const double v = reduce_partials(part);
-  if (threadIdx.x == 0) st->rr = v;
+  if (threadIdx.x == 0) {
+    st->rr = v;
+    if (!st->pcg) st->rz = v;
+  }
 }
 cudaError_t launch_cg_set_rr(const double* partials, CGState* st, cudaStream_t s) {
   count_launch();
@@ -409,7 +436,11 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr_fused(T* __restrict__ x, 
   v = block_sum(v);
   if (threadIdx.x == 0) {
     st->rr_new = v;
-    st->beta = (st->rr > 0.0) ? v / st->rr : 0.0;
+    if (!st->pcg) {
+      st->beta = (st->rr > 0.0) ? v / st->rr : 0.0;
+      st->rz_prev = st->rz;
+      st->rz = v;
+    }
     st->rr = v;
     *counter = 0u;
   }
@@ -425,86 +456,6 @@ template cudaError_t launch_cg_xr_fused<double>(double*, double*, const double*,
                                                 double*, unsigned*, cudaStream_t);
 template cudaError_t launch_cg_xr_fused<float>(float*, float*, const float*, const float*, CGState*, long long,
                                                double*, unsigned*, cudaStream_t);
-
-// pAp = sum(partials); alpha = rr / pAp  (0 and flag on breakdown or rr == 0)
-__global__ void k_cg_alpha(const double* part, CGState* st) {
-  const double v = reduce_partials(part);
-  if (threadIdx.x == 0) {
-    st->pAp = v;
-    double al = 0.0;
-    if (st->rr > 0.0) {
-      if (v > 0.0 && isfinite(v))
-        al = st->rr / v;
-      else
-        st->flag = 1;
-    }
-    st->alpha = al;
-  }
-}
-cudaError_t launch_cg_alpha(const double* partials, CGState* st, cudaStream_t s) {
-  count_launch();
-  k_cg_alpha<<<1, kRedThreads, 0, s>>>(partials, st);
-  return cudaGetLastError();
-}
-
-// x += alpha p, r -= alpha Ap, partial r.r
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_cg_xr(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                                                      const T* __restrict__ Ap, const CGState* st, long long n,
-                                                      double* __restrict__ part) {
-  const T al = (T)st->alpha;
-  DotAcc<T> acc;
-  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
-    x[i] += al * p[i];
-    const T ri = r[i] - al * Ap[i];
-    r[i] = ri;
-    acc.add(ri, ri);
-  }
-  const double v = block_sum(acc.value());
-  if (threadIdx.x == 0) part[blockIdx.x] = v;
-}
-template <typename T>
-cudaError_t launch_cg_xr(T* x, T* r, const T* p, const T* Ap, CGState* st, long long n, double* partials,
-                         cudaStream_t s) {
-  count_launch();
-  k_cg_xr<T><<<kRedBlocks, kRedThreads, 0, s>>>(x, r, p, Ap, st, n, partials);
-  return cudaGetLastError();
-}
-template cudaError_t launch_cg_xr<double>(double*, double*, const double*, const double*, CGState*, long long,
-                                          double*, cudaStream_t);
-template cudaError_t launch_cg_xr<float>(float*, float*, const float*, const float*, CGState*, long long, double*,
-                                         cudaStream_t);
-
-// rr_new = sum(partials); beta = rr_new / rr; rr = rr_new
-__global__ void k_cg_beta(const double* part, CGState* st) {
-  const double v = reduce_partials(part);
-  if (threadIdx.x == 0) {
-    st->rr_new = v;
-    st->beta = (st->rr > 0.0) ? v / st->rr : 0.0;
-    st->rr = v;
-  }
-}
-cudaError_t launch_cg_beta(const double* partials, CGState* st, cudaStream_t s) {
-  count_launch();
-  k_cg_beta<<<1, kRedThreads, 0, s>>>(partials, st);
-  return cudaGetLastError();
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_cg_p(T* __restrict__ p, const T* __restrict__ r, const CGState* st,
-                                                     long long n) {
-  const T be = (T)st->beta;
-  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads)
-    p[i] = r[i] + be * p[i];
-}
-template <typename T>
-cudaError_t launch_cg_p(T* p, const T* r, const CGState* st, long long n, cudaStream_t s) {
-  count_launch();
-  k_cg_p<T><<<kRedBlocks, kRedThreads, 0, s>>>(p, r, st, n);
-  return cudaGetLastError();
-}
-template cudaError_t launch_cg_p<double>(double*, const double*, const CGState*, long long, cudaStream_t);
-template cudaError_t launch_cg_p<float>(float*, const float*, const CGState*, long long, cudaStream_t);
 
 // ------------------------------------------------------------ elementwise
 #define RK_GRID_LOOP(i, n)                                                             \

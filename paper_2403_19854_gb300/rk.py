@@ -27,8 +27,8 @@ EXPORTED = ["rk_default_solve_opts", "rk_supported_length", "rk_setup", "rk_sing
             "rk_rhs", "rk_eval_u", "rk_eval_u_transpose", "rk_get_b", "rk_get_shape", "rk_solve",
             "rk_solve_adjoint", "rk_destroy", "rk_status_string", "rk_last_error_message",
             "rk_kernel_launches", "rk_profile_enable", "rk_profile_read", "rk_profile_class_name",
-            "rk_solve_vjp", "rk_clone", "rk_solve_batched"]
-PROF_CLASSES = 11
+            "rk_solve_vjp", "rk_clone", "rk_solve_batched", "rk_apply_precond"]
+PROF_CLASSES = 12
 
 
 class RKError(RuntimeError):
@@ -44,7 +44,8 @@ class Grid(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("x0_given", ctypes.c_int32), ("fp64_finish", ctypes.c_int32)]
+                ("x0_given", ctypes.c_int32), ("fp64_finish", ctypes.c_int32),
+                ("precond", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class BatchItem(ctypes.Structure):
@@ -78,6 +79,7 @@ def lib():
     L.rk_setup.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, i32, f64, vp, ctypes.POINTER(vp)]
     L.rk_singular_nodes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.rk_apply_K.argtypes = [vp, vp, vp, i32, vp]
+    L.rk_apply_precond.argtypes = [vp, vp, vp, i32, vp]
     for name in ("rk_rhs", "rk_eval_u", "rk_eval_u_transpose"):
         getattr(L, name).argtypes = [vp, vp, vp, vp]
     L.rk_get_b.argtypes = [vp, vp, vp]
@@ -153,6 +155,8 @@ def default_opts(**kw) -> SolveOpts:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": RK_PREC_FP64, "mixed": RK_PREC_MIXED}[v]
+        if k == "precond" and isinstance(v, str):
+            v = {"none": 0, "spectral": 1}[v]
         setattr(o, k, v)
     return o
 
@@ -240,6 +244,17 @@ class Handle:
         pf, kf = _ptr(f)
         _check(lib().rk_apply_K(self._h, pd, pf, dt, stream if stream is not None else _stream(d)))
         return f
+
+    def apply_precond(self, r, z=None, stream=None):
+        """z = M^{-1} r, the spectral preconditioner (float32 -> FP32 path, float64 -> FP64)."""
+        is32 = (str(r.dtype).endswith("float32"))
+        dt = RK_F32 if is32 else RK_F64
+        if z is None:
+            z = _like(r, dt, self.nbox)
+        pr, kr = _ptr(r)
+        pz, kz = _ptr(z)
+        _check(lib().rk_apply_precond(self._h, pr, pz, dt, stream if stream is not None else _stream(r)))
+        return z
 
     def _unary(self, fn, x, out, stream):
         if out is None:
