@@ -4,7 +4,9 @@
 * rk_solve_adjoint against autograd through poisson_solve (rk_solve_vjp backward);
 * both against central finite differences on seeded directions: J is an exact
   quadratic in (r, g), so (J(t + e d) - J(t - e d)) / 2e equals grad . d up to the
-  solve tolerance, for any e.
+  solve tolerance, for any e.  3 directions with plain CG solves, and the 32 seeded
+  directions of the workload with preconditioned solves (the solver only evaluates
+  J; any solve to the tolerance gives the same quadratic).
 """
 import numpy as np
 import pytest
@@ -69,3 +71,28 @@ def test_adjoint_central_differences(problem, prec):
               - _J(H, t, t["r"] - eps * dr, t["g"] - eps * dg, prec)) / (2 * eps)
         an = float((gr * dr).sum() + (gg * dg).sum())
         assert an == pytest.approx(fd, rel=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_adjoint_32_directions(problem, prec):
+    p, H, t = problem
+    J, gr, gg, info = H.solve_adjoint(t["r"], t["g"], t["ut"], precision=prec, tol=1e-12, precond="spectral")
+    Jp, grp, ggp, _ = H.solve_adjoint(t["r"], t["g"], t["ut"], precision=prec, tol=1e-12)
+    # the gradient does not depend on the solver used for it
+    assert float((gr - grp).norm() / grp.norm()) < 1e-8 and float((gg - ggp).norm() / ggp.norm()) < 1e-8
+
+    def Jp_(r, g):
+        _, u, _ = H.solve(r, g, precision=prec, tol=1e-12, precond="spectral")
+        e = (u - t["ut"]) * t["chi"]
+        return 0.5 * float((e * e).sum())
+
+    rng = np.random.default_rng(20240328 + 4032)
+    worst = 0.0
+    for _ in range(32):
+        dr = torch.as_tensor(rng.standard_normal(p.nbox), device=DEV) * t["chi"]
+        dg = torch.as_tensor(rng.standard_normal(p.nbox), device=DEV) * t["chi_gamma"]
+        eps = 1e-3 * float(t["r"].norm()) / float(dr.norm())
+        fd = (Jp_(t["r"] + eps * dr, t["g"] + eps * dg) - Jp_(t["r"] - eps * dr, t["g"] - eps * dg)) / (2 * eps)
+        an = float((gr * dr).sum() + (gg * dg).sum())
+        worst = max(worst, abs(an - fd) / abs(fd))
+    assert worst < 1e-6

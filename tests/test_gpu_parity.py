@@ -184,6 +184,30 @@ def test_full_size_sampled_parity(nb, a, deg):
         assert rel(bg[i][:, sample].T, bo[:, i, :]) < TOL64
 
 
+def test_full_size_sampled_parity_spheres256_quadratic():
+    """The embedded-domain workload at full size: 12 spheres in a 256^3 box, quadratic
+    basis, a = 3h.  K.u (FP64, FP32) and b at sampled nodes (interior, boundary and
+    near-boundary), each recomputed by the oracle from scratch."""
+    p = W.spheres_problem(n_box=256, n_spheres=12, a_tilde=3.0, degree=2)
+    H = rk.Handle.from_problem(p, device=DEV)
+    rng = np.random.default_rng(256)
+    inside = np.flatnonzero(p.chi)
+    bnd = np.flatnonzero(p.chi_gamma)
+    sample = np.unique(np.concatenate([rng.choice(inside, 40, replace=False), rng.choice(bnd, 24, replace=False)]))
+    d = W.random_field(p.nbox, 9) * p.chi
+    f64 = np_(H.apply_K(tdev(d)))
+    fo = apply_K_sampled(p.n, p.h, 3.0, 2, p.chi, p.V, d, sample)
+    assert rel(f64[sample], fo) < TOL64
+    f32 = np_(H.apply_K(tdev(d.astype(np.float32)))).astype(np.float64)
+    fo32 = apply_K_sampled(p.n, p.h, 3.0, 2, p.chi, p.V, d.astype(np.float32).astype(np.float64), sample)
+    assert rel(f32[sample], fo32) < 10 * TOL32
+    bg = np_(H.get_b(torch.empty(4 * p.s * p.nbox, dtype=torch.float64, device=DEV)))
+    bo = b_sampled(p.n, p.h, 3.0, 2, p.chi, sample)
+    for i in range(4):
+        assert rel(bg[i][:, sample].T, bo[:, i, :]) < TOL64
+    H.close()
+
+
 def test_gap_narrower_than_support_is_rejected():
     """A domain that touches its periodic image within the support is refused (Eq. 66).
     At a = 2h the reach is one node (phi(2h) = 0), so one empty node suffices; with
