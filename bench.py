@@ -106,6 +106,20 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate_over_ranks(ms, units, world, device):
+    """Whole-job figures of independent replicas: the slowest rank's time and the
+    units (DOF x K.u applications) of all ranks.  Returns (max ms, total units)."""
+    if world <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ------------------------------------------------------------------- oracle
 def oracle_kd_rate(n_box=64, a_tilde=2.5, reps=3):
     """FP64 oracle matrix-free K.d (neighbour loops, one host core) on a bounded cube
@@ -254,7 +268,7 @@ def run_ours(args):
     barrier()
     L1 = rk.kernel_launches()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
+    ms_local = e0.elapsed_time(e1)
     # one more step with CUDA events around every kernel class on the launching
     # stream (this disables the graph replay of CG chunks, so it is kept out of
     # the timed steps): per-kernel durations for the roofline
@@ -266,13 +280,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     profiled_ms = p0.elapsed_time(p1)
     profs = [pr]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     matvecs = sum(i["matvec_f32"] + i["matvec_f64"] for i in infos)
-    value = world * n_dof * matvecs / (ms / 1e3)
+    ms, units = aggregate_over_ranks(ms_local, float(n_dof * matvecs), world, dev)
+    value = units / (ms / 1e3)
     u_mixed = u.cpu().numpy().copy()
 
     # kernel profile over the timed steps: dominant class and its roofline
@@ -394,7 +404,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         e2e_mv += ie["matvec_f32"] + ie["matvec_f64"]
-    e2e_value = n_dof * e2e_mv / (sum(e2e_ms) / 1e3) * world
+    e2e_total_ms, e2e_units = aggregate_over_ranks(sum(e2e_ms), float(n_dof * e2e_mv), world, dev)
+    e2e_value = e2e_units / (e2e_total_ms / 1e3)
     h2d = p.nbox * (1 + 1 + 8 + 8 + 8)
     d2h = p.nbox * (8 + 8)
 
