@@ -65,6 +65,23 @@ cudaError_t launch_strided(int axis, const PassArgs<T>& a, cudaStream_t s, const
   return cudaGetLastError();
 }
 
+// x split: rows arrive by bulk async copies when the pass carries the fused CG
+// direction update (two fields, r and p, per row: 0.099 -> 0.072 ms at 256^3),
+// a row is a whole number of 16-byte units and every field starts on a 16-byte
+// boundary.  With one field per row (plain split, and the merge pass) per-thread
+// loads measured faster (0.060 vs 0.069 ms), so those keep them.
+template <typename T, int N, int LX>
+bool x_bulk_setup(PassArgs<T>& b) {
+  using X = XPass<T, N, LX>;
+  bool ok = X::BULK && b.n_groups == 1 && b.cg_r;
+  auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) % 16) == 0; };
+  for (int i = 0; i < kMaxIn; ++i)
+    if (b.in[i] && !aligned(b.in[i])) ok = false;
+  if ((b.cg_r && !aligned(b.cg_r)) || (b.cg_p && !aligned(b.cg_p))) ok = false;
+  b.xbulk = ok ? 1 : 0;
+  return ok;
+}
+
 template <typename T, int N>
 cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps) {
   if (axis == 0) {
@@ -72,11 +89,20 @@ cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMa
     using X = XPass<T, N, LX>;
     const long long npairs = ((long long)a.ny * a.nz) / 2;
     const unsigned nb = (unsigned)((npairs + LX - 1) / LX);
-    auto k = k_x_split<T, N, LX>;
-    cudaError_t e = set_smem(k, X::SMEM);
-    if (e != cudaSuccess) return e;
-    count_launch();
-    k<<<nb, X::THREADS, X::SMEM, s>>>(a);
+    PassArgs<T> b = a;
+    if (x_bulk_setup<T, N, LX>(b)) {
+      auto k = k_x_split<T, N, LX, true>;
+      cudaError_t e = set_smem(k, X::SMEM + 2 * X::TILE);
+      if (e != cudaSuccess) return e;
+      count_launch();
+      k<<<nb, X::THREADS, X::SMEM + 2 * X::TILE, s>>>(b);
+    } else {
+      auto k = k_x_split<T, N, LX, false>;
+      cudaError_t e = set_smem(k, X::SMEM);
+      if (e != cudaSuccess) return e;
+      count_launch();
+      k<<<nb, X::THREADS, X::SMEM, s>>>(b);
+    }
   } else {
     return launch_strided<T, N, false>(axis, a, s, maps);
   }

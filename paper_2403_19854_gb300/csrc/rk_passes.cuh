@@ -79,6 +79,7 @@ struct PassArgs {
   double* partials;           // MERGE: one partial p.Ap per block
   unsigned* counter;          // MERGE: blocks finished (the last one reduces and resets it)
   int* err;                   // set to 1 when a bounded wait for an input tile gave up
+  int xbulk;                  // x passes: rows arrive by bulk async copies (set by the launcher)
 };
 
 // ---------------------------------------------------------------- strided passes
@@ -323,7 +324,64 @@ struct XPass {
   using B = PaddedBuf<T, F::N1, F::N2>;
   static constexpr int P = F::P, R = F::R;
   static constexpr int THREADS = LX * P;
-  static constexpr size_t SMEM = sizeof(cpx<T>) * (size_t)B::SIZE * LX;
+  static constexpr size_t SMEM = (sizeof(cpx<T>) * (size_t)B::SIZE * LX + 127) / 128 * 128;
+  // Row tiles of the bulk-copy feed: the block's 2 LX rows are contiguous in
+  // memory; each row lands in shared memory with a 32-byte pad, so the two half
+  // warps (rows 2l and 2l+2) read from disjoint bank halves.  Possible when a row
+  // is a whole number of 16-byte units.
+  static constexpr bool BULK = (N * sizeof(T)) % 16 == 0;
+  static constexpr int ROWS = 2 * LX;
+  static constexpr int PITCH = N + 32 / (int)sizeof(T);
+  static constexpr size_t TILE = sizeof(T) * (size_t)ROWS * PITCH;
+  // resident blocks per SM the register allocation must allow
+  static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 4 : 3;
+};
+
+RK_DEV void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Bulk feed of the x passes: the rows [row0, row0 + rows) of up to two fields into
+// row tiles, completion on one mbarrier (one transaction per call).
+template <typename T, int N, int LX>
+struct XFeed {
+  using X = XPass<T, N, LX>;
+  uint64_t* bar;
+  uint32_t phase;
+  RK_DEV void init() {
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      mbar_init_fence();
+    }
+    RK_SYNC();
+  }
+  RK_DEV void issue(T* tileA, const T* srcA, T* tileB, const T* srcB, long long row0, int rows) {
+    if (threadIdx.x < 32) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, (uint32_t)(rows * N * sizeof(T) * (srcB ? 2 : 1)));
+      }
+      __syncwarp();
+      for (int j = threadIdx.x; j < rows; j += 32) {
+        bulk_g2s(tileA + j * X::PITCH, srcA + (row0 + j) * N, (uint32_t)(N * sizeof(T)), bar);
+        if (srcB) bulk_g2s(tileB + j * X::PITCH, srcB + (row0 + j) * N, (uint32_t)(N * sizeof(T)), bar);
+      }
+    }
+  }
+  // false (uniformly) when the bounded wait gave up; the caller returns
+  RK_DEV bool wait(int* err) {
+    const bool ok = mbar_wait(bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0 && err) atomicExch(err, 1);
+      mbar_wait(bar, phase ^ 1u);
+      return false;
+    }
+    return true;
+  }
 };
 
 template <typename T>
@@ -400,11 +458,19 @@ __device__ __forceinline__ void cg_pap_reduce(double v, const PassArgs<T>& a) {
   }
 }
 
-template <typename T, int N, int LX>
-__global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_split(const PassArgs<T> a) {
+// FEED: the rows of r and p arrive by bulk async copies (the CG variant); a
+// separate instantiation, so that the plain variant keeps the default shared
+// memory carve-out (its twiddle and multiplier loads live in L1).
+template <typename T, int N, int LX, bool FEED>
+__global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN_BLOCKS)
+    k_x_split(const PassArgs<T> a) {
   using X = XPass<T, N, LX>;
   using F = typename X::F;
-  RK_DYN_SMEM(cpx<T>, sm);
+  RK_DYN_SMEM(unsigned char, smem);
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem);
+  T* tileA = reinterpret_cast<T*>(smem + X::SMEM);
+  T* tileB = tileA + X::ROWS * X::PITCH;
+  __shared__ uint64_t bar;
   const int t = threadIdx.x % X::P, l = threadIdx.x / X::P;
   const long long q = (long long)blockIdx.x * LX + l;  // row pair
   const long long npairs = ((long long)a.ny * a.nz) / 2;
@@ -412,6 +478,18 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_split(const Pass
   const long long r0 = 2 * q * a.nx, r1 = r0 + a.nx;
   typename X::B buf{sm + (size_t)l * X::B::SIZE};
   cpx<T> v[X::R], w[X::R];
+  const bool bulk = FEED && X::BULK && a.xbulk && a.n_groups == 1;
+  const long long row0 = 2LL * blockIdx.x * LX;
+  if (bulk) {
+    XFeed<T, N, LX> feed{&bar, 0u};
+    feed.init();
+    const long long nrows = (long long)a.ny * a.nz;
+    const int rows = (int)((nrows - row0) < X::ROWS ? (nrows - row0) : X::ROWS);
+    feed.issue(tileA, a.cg_r ? a.cg_r : a.in[a.g_io[0]], tileB, a.cg_r ? a.cg_p : nullptr, row0, rows);
+    if (!feed.wait(a.err)) return;
+  }
+  const T* ra = tileA + (2 * l) * X::PITCH;  // this thread's rows in the tiles
+  const T* rb = ra + X::PITCH;
   for (int g = 0; g < a.n_groups; ++g) {
     const T* in = a.in[a.g_io[g]];
     if (a.cg_r) {
@@ -422,8 +500,13 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_split(const Pass
         const int xp = F::nat_pos(t, r);
         T p0 = (T)0, p1 = (T)0;
         if (ok) {
-          p0 = a.cg_r[r0 + xp] + be * a.cg_p[r0 + xp];
-          p1 = a.cg_r[r1 + xp] + be * a.cg_p[r1 + xp];
+          if (bulk) {
+            p0 = ra[xp] + be * tileB[(2 * l) * X::PITCH + xp];
+            p1 = rb[xp] + be * tileB[(2 * l + 1) * X::PITCH + xp];
+          } else {
+            p0 = a.cg_r[r0 + xp] + be * a.cg_p[r0 + xp];
+            p1 = a.cg_r[r1 + xp] + be * a.cg_p[r1 + xp];
+          }
           a.cg_p[r0 + xp] = p0;
           a.cg_p[r1 + xp] = p1;
         }
@@ -435,16 +518,17 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_split(const Pass
 #pragma unroll
       for (int r = 0; r < X::R; ++r) {
         const int xp = F::nat_pos(t, r);
-        v[r] = ok ? cmk(RK_LDG(in + r0 + xp) * (T)msk[(2 * l) * N + xp], RK_LDG(in + r1 + xp) * (T)msk[(2 * l + 1) * N + xp])
-                  : cmk((T)0, (T)0);
+        const T x0 = ok ? (bulk ? ra[xp] : RK_LDG(in + r0 + xp)) : (T)0;
+        const T x1 = ok ? (bulk ? rb[xp] : RK_LDG(in + r1 + xp)) : (T)0;
+        v[r] = cmk(x0 * (T)msk[(2 * l) * N + xp], x1 * (T)msk[(2 * l + 1) * N + xp]);
       }
     } else {
 #pragma unroll
       for (int r = 0; r < X::R; ++r) {
         const int xp = F::nat_pos(t, r);
-        v[r] = ok ? cmk(RK_LDG(in + r0 + xp) * mask_of<T>(a.in_mask, r0 + xp),
-                        RK_LDG(in + r1 + xp) * mask_of<T>(a.in_mask, r1 + xp))
-                  : cmk((T)0, (T)0);
+        const T x0 = ok ? (bulk ? ra[xp] : RK_LDG(in + r0 + xp)) : (T)0;
+        const T x1 = ok ? (bulk ? rb[xp] : RK_LDG(in + r1 + xp)) : (T)0;
+        v[r] = ok ? cmk(x0 * mask_of<T>(a.in_mask, r0 + xp), x1 * mask_of<T>(a.in_mask, r1 + xp)) : cmk((T)0, (T)0);
       }
     }
     F::forward(v, t, buf, a.tw);
