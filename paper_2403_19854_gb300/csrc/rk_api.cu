@@ -309,6 +309,7 @@ PassArgs<T> pass_base(const rk_handle* h, int axis) {
   PassArgs<T> a;
   memset(&a, 0, sizeof(a));
   a.err = h->err_dev;
+  a.coef_rows = 2 * h->degree + 1;
   a.coef = coef_of<T>(h, axis);
   a.tw = tw_of<T>(h, axis);
   a.nx = h->n[0];

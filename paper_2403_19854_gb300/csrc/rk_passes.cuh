@@ -66,6 +66,7 @@ struct PassArgs {
   const T* coef;              // spectral multipliers of this axis, [mmax+1][N]
   const cpx<T>* tw;           // twiddles of this axis, [N]
   int reflect;
+  int coef_rows;              // rows of coef (2 degree + 1); 0: not staged in shared memory
   const uint8_t* in_mask;     // optional: inputs multiplied by mask (x pass only)
   const uint8_t* out_mask;    // optional: outputs multiplied by mask (x pass only)
   int nx, ny, nz;
@@ -122,7 +123,26 @@ struct Strided {
   static constexpr int C16 = ROW * (int)sizeof(T) / 16;  // 16-byte chunks per row
   static constexpr size_t SMEM_BUF = sizeof(cpx<T>) * (size_t)N * L;
   static constexpr size_t SMEM_TILE = sizeof(T) * (size_t)N * ROW;
-  static constexpr size_t SMEM = SMEM_BUF + SMEM_TILE;
+  // FP32 split: the axis' multiplier rows (up to 5) and twiddles are copied to
+  // shared memory once per block (the large shared-memory carve-out of these
+  // kernels leaves little L1 for them; 2-3 % faster)
+  static constexpr bool STAGE = sizeof(T) == 4;
+  static constexpr int COEF_ROWS_MAX = 5;
+  static constexpr size_t SMEM_CT = STAGE ? sizeof(T) * (size_t)COEF_ROWS_MAX * N + sizeof(cpx<T>) * (size_t)N : 0;
+  static constexpr size_t SMEM = SMEM_BUF + SMEM_TILE + SMEM_CT;
+  // copy coef / tw to shared memory; returns the pointers the block should use
+  RK_DEV static void stage(const PassArgs<T>& a, unsigned char* smem, const T** coef, const cpx<T>** tw) {
+    *coef = a.coef;
+    *tw = a.tw;
+    if (!STAGE || a.coef_rows <= 0 || a.coef_rows > COEF_ROWS_MAX) return;
+    T* cs = reinterpret_cast<T*>(smem + SMEM_TILE + SMEM_BUF);
+    cpx<T>* ts = reinterpret_cast<cpx<T>*>(cs + (size_t)COEF_ROWS_MAX * N);
+    for (int i = threadIdx.x; i < a.coef_rows * N; i += THREADS) cs[i] = a.coef[i];
+    for (int i = threadIdx.x; i < N; i += THREADS) ts[i] = a.tw[i];
+    RK_SYNC();
+    *coef = cs;
+    *tw = ts;
+  }
 
   // Copy rows src[x0 + j * line_stride + (0 .. nvalid-1)], j in [0, N), into tile
   // (zero-filled beyond nvalid).  a16: every row starts on a 16-byte boundary.
@@ -233,6 +253,9 @@ __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::M
   };
   long long tile = blockIdx.x;
   if (tile < ntiles) prefetch(tile, 0);
+  const T* coef;
+  const cpx<T>* tw;
+  S::stage(a, smem, &coef, &tw);
   cpx<T> v[S::R], w[S::R];
   for (; tile < ntiles; tile += gridDim.x) {
     const int x0 = (int)(tile % nbx) * S::ROW;
@@ -247,12 +270,12 @@ __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::M
         prefetch(tile, g + 1);
       else if (tile + gridDim.x < ntiles)
         prefetch(tile + gridDim.x, 0);
-      F::forward(v, t, buf, a.tw);
+      F::forward(v, t, buf, tw);
       for (int q = a.g_begin[g]; q < a.g_begin[g + 1]; ++q) {
         const int m = a.term_m[q];
 #pragma unroll
-        for (int r = 0; r < S::R; ++r) w[r] = spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
-        F::inverse(w, t, buf, a.tw);
+        for (int r = 0; r < S::R; ++r) w[r] = spec_mul(v[r], coef, N, m, F::spec_idx(t, r), a.reflect);
+        F::inverse(w, t, buf, tw);
         T* out = a.out[a.term_io[q]];
         if (ok)
 #pragma unroll
@@ -284,6 +307,10 @@ __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::M
   };
   long long tile = blockIdx.x;
   if (tile < ntiles) prefetch(tile, 0);
+  // multipliers and twiddles read through L1 (staging them in shared memory, as
+  // the split pass does, measured slower here)
+  const T* coef = a.coef;
+  const cpx<T>* tw = a.tw;
   cpx<T> v[S::R], acc[S::R];
   for (; tile < ntiles; tile += gridDim.x) {
     const int x0 = (int)(tile % nbx) * S::ROW;
@@ -302,11 +329,11 @@ __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::M
           prefetch(tile, q + 1);
         else if (tile + gridDim.x < ntiles)
           prefetch(tile + gridDim.x, 0);
-        F::forward(v, t, buf, a.tw);
+        F::forward(v, t, buf, tw);
 #pragma unroll
-        for (int r = 0; r < S::R; ++r) acc[r] = acc[r] + spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
+        for (int r = 0; r < S::R; ++r) acc[r] = acc[r] + spec_mul(v[r], coef, N, m, F::spec_idx(t, r), a.reflect);
       }
-      F::inverse(acc, t, buf, a.tw);
+      F::inverse(acc, t, buf, tw);
       T* out = a.out[a.g_io[g]];
       if (ok)
 #pragma unroll
