@@ -209,6 +209,51 @@ rk_status rk_solve(rk_handle* h, const double* r, const double* g, double* d, do
                    const rk_solve_opts* opts, rk_solve_info* info, void* stream);
 
 /*
+ * rk_boundary_rhs -- f^q of Alg. A.1, the boundary integral of Eq. 28 in the
+ * convolutional form of Eq. A.4-A.5 (DNI on the boundary nodes, Eq. A.2):
+ *   f^q = chi o F^{-1}[ sum_p F(chi o A o b0_p o q) o F(Hbar^a_p) ]
+ * q: Neumann data at the nodes of Gamma_q; A: quadrature weight (area) of each
+ * boundary node, 0 elsewhere (Eq. A.6-A.7).  FP64 box arrays, host or device.
+ * fq: FP64 box array, 0 off chi.
+ */
+rk_status rk_boundary_rhs(rk_handle* h, const double* q, const double* A, double* fq, void* stream);
+
+/*
+ * rk_solve_neumann -- Alg. 5 with Neumann data as well: the right-hand side of
+ * Eq. 25 becomes f^r + f^q (rk_boundary_rhs) before the strong Dirichlet data
+ * g on Gamma_g enter (Eq. 29).  Arguments as rk_solve, plus q and A as in
+ * rk_boundary_rhs (both required).
+ */
+rk_status rk_solve_neumann(rk_handle* h, const double* r, const double* g, const double* q, const double* A, double* d,
+                           double* u, const rk_solve_opts* opts, rk_solve_info* info, void* stream);
+
+/*
+ * Time-dependent problems (Appendix C; diffusion u_t = lap u + r, Eq. C.1-C.4:
+ * M d' + K d = f^r + f^q).
+ *
+ * rk_apply_M -- f^m = M v, the consistent mass action of Alg. C.1 (Eq. C.7-C.12):
+ *   A^0 = sum_q b0_q o F^{-1}[F(chi o v) F(H^a_q)],  f^m = chi o F^{-1}[sum_p F(chi V b0_p A^0) F(Hbar^a_p)].
+ *   v, fm: box arrays of dtype RK_F64 or RK_F32, host or device.
+ * rk_lumped_mass -- M^l, the row sums of M (Alg. C.2, Eq. C.9-C.13), FP64.
+ * rk_transient_explicit -- Alg. C.3 with forward Euler and the lumped mass:
+ *   n_steps times  d <- d + dt (M^l)^{-1} (f - K d) on the free nodes chi_Omega,
+ *   with d = g on Gamma_g (g may be NULL: 0) and 0 off chi.  f = f^r + f^q (rk_rhs,
+ *   rk_boundary_rhs), fixed over the steps; call with n_steps = 1 per step when it
+ *   changes.  d: FP64 box array, in/out.  Stable for dt below 2 / lam_max((M^l)^{-1} K)
+ *   (not checked).
+ * rk_transient_implicit -- Alg. C.4 with backward Euler: n_steps times
+ *   (M + dt K) d_{k+1} = M d_k + dt f on the free nodes, d = g on Gamma_g, each step
+ *   by FP64 CG to opts->tol (relative residual of the step).  info: total CG
+ *   iterations, steps (outer), FP64 operator applications, worst step residual.
+ */
+rk_status rk_apply_M(rk_handle* h, const void* v, void* fm, int32_t dtype, void* stream);
+rk_status rk_lumped_mass(rk_handle* h, double* ml, void* stream);
+rk_status rk_transient_explicit(rk_handle* h, const double* f, const double* g, double dt, int32_t n_steps, double* d,
+                                void* stream);
+rk_status rk_transient_implicit(rk_handle* h, const double* f, const double* g, double dt, int32_t n_steps, double* d,
+                                const rk_solve_opts* opts, rk_solve_info* info, void* stream);
+
+/*
  * rk_solve_adjoint -- gradient of J = 1/2 sum_{chi} (u^h - u_target)^2 with respect
  * to the source r and the Dirichlet data g, for the solve of rk_solve.  The forward
  * solve is recomputed from (r, g) (nothing is kept between calls); one adjoint

@@ -167,6 +167,9 @@ struct rk_handle {
   SymbolArgs<double> sym64;
   float* mult32 = nullptr;   // z SYM multiplier tables (owned by the set-up handle)
   double* mult64 = nullptr;
+  // transient solvers (Appendix C): 5 FP64 and 1 FP32 scratch fields, on first use
+  double* trans64 = nullptr;
+  float* trans32 = nullptr;
   // staging of host arrays
   double* stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   unsigned long long* counters = nullptr;  // singular count, first singular
@@ -1250,8 +1253,15 @@ rk_status check_opts(const rk_solve_opts& o) {
 
 // The forward solve of Alg. 5: d = d_Gamma + x, x on chi_Omega.  Vectors in the
 // handle: F = v64(4), d0 = v64(5).
+// f^q of Alg. A.1 (Eq. A.4-A.5): chi o sum_p Hbar_p (*) (chi A b0_p q)
+rk_status boundary_rhs(rk_handle* h, const double* q, const double* A, double* fq, cudaStream_t s) {
+  return op_UT<double>(h, q, fq, A, h->chi, s);
+}
+
+// q, A (optional, both or neither): Neumann flux and boundary quadrature weights;
+// then F also holds f^q (Eq. 25)
 rk_status forward_solve(rk_handle* h, const double* r, const double* g, double* d, const rk_solve_opts& o,
-                        rk_solve_info* info, cudaStream_t s) {
+                        rk_solve_info* info, cudaStream_t s, const double* q = nullptr, const double* A = nullptr) {
   const long long n = h->nbox;
   double* F = h->v64(4);
   double* d0 = h->v64(5);
@@ -1262,8 +1272,12 @@ rk_status forward_solve(rk_handle* h, const double* r, const double* g, double* 
     RK_CK(launch_dirichlet_d0(d0, g, h->chi_gamma, n, s));
   else
     RK_CK(launch_fill<double>(d0, 0.0, n, s));
-  // f^r (Alg. 4) and F = chi_Omega o (f^r - K d_Gamma)
+  // f^r (Alg. 4), f^q (Alg. A.1) and F = chi_Omega o (f^r + f^q - K d_Gamma)
   RK_TRY(op_UT<double>(h, r, t0, h->chiV64, nullptr, s));
+  if (q && A) {
+    RK_TRY(boundary_rhs(h, q, A, h->v64(8), s));  // v64(8) is free until the CG starts
+    RK_CK(launch_add(t0, t0, h->v64(8), n, s));
+  }
   RK_TRY(op_K<double>(h, d0, F, h->chi, h->chi_omega, s));
   info->matvec_f64++;
   RK_CK(launch_masked_diff(F, t0, F, h->chi_omega, n, s));
@@ -1274,6 +1288,143 @@ rk_status forward_solve(rk_handle* h, const double* r, const double* g, double* 
   rk_status st = solve_masked(h, F, x, o, info, s);
   RK_CK(launch_add(d, d0, x, n, s));
   return st;
+}
+
+// ------------------------------------------------------ time-dependent terms
+// Appendix C: f^m = M v (Alg. C.1, Eq. C.11-C.12) is the chain of Alg. 3 followed
+// by that of Alg. 4: A^0 = sum_q b0_q (H_q (*) chi v), f^m = chi o sum_p Hbar_p (*)
+// (chi V b0_p A^0).  The lumped mass (Alg. C.2, Eq. C.13) is Alg. 4 applied to 1.
+template <typename T>
+T* trans_scratch(rk_handle* h);
+template <>
+double* trans_scratch<double>(rk_handle* h) { return h->trans64; }
+template <>
+float* trans_scratch<float>(rk_handle* h) { return h->trans32; }
+
+rk_status ensure_transient(rk_handle* h) {
+  if (!h->trans64) RK_TRY(h->alloc(&h->trans64, (size_t)5 * h->nbox));
+  if (!h->trans32) RK_TRY(h->alloc(&h->trans32, (size_t)h->nbox));
+  return RK_OK;
+}
+
+template <typename T>
+rk_status op_M(rk_handle* h, const T* v, T* fm, cudaStream_t s) {
+  RK_TRY(ensure_transient(h));
+  T* a0 = trans_scratch<T>(h);  // scratch 0
+  RK_TRY(op_U<T>(h, v, a0, s));
+  return op_UT<T>(h, a0, fm, chiV<T>(h), nullptr, s);
+}
+
+rk_status lumped_mass(rk_handle* h, double* ml, cudaStream_t s) {
+  RK_TRY(ensure_transient(h));
+  double* one = h->trans64 + (size_t)4 * h->nbox;  // scratch 4
+  RK_CK(launch_fill<double>(one, 1.0, h->nbox, s));
+  return op_UT<double>(h, one, ml, h->chiV64, nullptr, s);
+}
+
+// Alg. C.3 with forward Euler: d += dt (M^l)^{-1} (f - K d) on chi_Omega, d = g on Gamma_g
+rk_status transient_explicit(rk_handle* h, const double* f, const double* g, double dt, int n_steps, double* d,
+                             cudaStream_t s) {
+  RK_TRY(ensure_transient(h));
+  const long long n = h->nbox;
+  double* ml = h->trans64 + (size_t)1 * n;
+  double* Kd = h->trans64 + (size_t)2 * n;
+  RK_TRY(lumped_mass(h, ml, s));
+  if (g) RK_CK(launch_dirichlet_d0(h->trans64 + (size_t)3 * n, g, h->chi_gamma, n, s));
+  // d = g on Gamma_g, 0 off chi (d keeps its free values)
+  if (g) {
+    RK_CK(launch_mask(d, d, h->chi_omega, n, s));
+    RK_CK(launch_add(d, d, h->trans64 + (size_t)3 * n, n, s));
+  } else {
+    RK_CK(launch_mask(d, d, h->chi_omega, n, s));
+  }
+  for (int k = 0; k < n_steps; ++k) {
+    RK_TRY(op_K<double>(h, d, Kd, h->chi, h->chi_omega, s));
+    RK_CK(launch_explicit_step(d, f, Kd, ml, h->chi_omega, dt, n, s));
+  }
+  return RK_OK;
+}
+
+// Alg. C.4 with backward Euler: (M + dt K) d_{k+1} = M d_k + dt f, d = g on
+// Gamma_g; each step solved by FP64 CG on the free nodes, A = chi_Omega o (M + dt K)
+rk_status transient_implicit(rk_handle* h, const double* f, const double* g, double dt, int n_steps, double* d,
+                             const rk_solve_opts& o, rk_solve_info* info, cudaStream_t s) {
+  RK_TRY(ensure_transient(h));
+  RK_TRY(ensure_solver(h));
+  const long long n = h->nbox;
+  double* x = h->v64(0);   // free part of d
+  double* r = h->v64(1);
+  double* p = h->v64(2);
+  double* Ap = h->v64(3);
+  double* b = h->v64(4);
+  double* dG = h->v64(5);  // g on Gamma_g
+  double* t = h->v64(6);
+  double* t2 = h->trans64 + (size_t)1 * n;
+  auto apply_A = [&](const double* v, double* out) -> rk_status {
+    RK_TRY(op_M<double>(h, v, out, s));
+    RK_TRY(op_K<double>(h, v, t2, h->chi_omega, h->chi_omega, s));
+    RK_CK(launch_axpby(out, dt, t2, 1.0, n, s));
+    RK_CK(launch_mask(out, out, h->chi_omega, n, s));
+    info->matvec_f64++;
+    return RK_OK;
+  };
+  auto dot = [&](const double* a, const double* c, double* out) -> rk_status {
+    RK_CK(launch_dot<double, double>(a, c, n, h->partials, h->dscal, s));
+    return read_scalar(h, h->dscal, out, s);
+  };
+  if (g)
+    RK_CK(launch_dirichlet_d0(dG, g, h->chi_gamma, n, s));
+  else
+    RK_CK(launch_fill<double>(dG, 0.0, n, s));
+  // dt K d_Gamma is the same every step
+  double* KdG = h->trans64 + (size_t)2 * n;
+  RK_TRY(op_K<double>(h, dG, KdG, h->chi, h->chi_omega, s));
+  RK_CK(launch_mask(x, d, h->chi_omega, n, s));
+  for (int step = 0; step < n_steps; ++step) {
+    // b = chi_Omega o (M x_k + dt f - dt K d_Gamma)   (M d_Gamma cancels between sides)
+    RK_TRY(op_M<double>(h, x, b, s));
+    RK_CK(launch_axpby(b, dt, f, 1.0, n, s));
+    RK_CK(launch_axpby(b, -dt, KdG, 1.0, n, s));
+    RK_CK(launch_mask(b, b, h->chi_omega, n, s));
+    double bn;
+    RK_TRY(dot(b, b, &bn));
+    bn = std::sqrt(bn);
+    if (bn == 0.0) {
+      RK_CK(launch_fill<double>(x, 0.0, n, s));
+      continue;
+    }
+    RK_TRY(apply_A(x, Ap));
+    RK_CK(launch_sub(r, b, Ap, n, s));
+    RK_CK(launch_copy<double>(p, r, n, s));
+    double rr;
+    RK_TRY(dot(r, r, &rr));
+    int it = 0;
+    while (std::sqrt(rr) > o.tol * bn && it < o.max_iter) {
+      RK_TRY(apply_A(p, Ap));
+      double pAp;
+      RK_TRY(dot(p, Ap, &pAp));
+      if (!(pAp > 0.0) || !std::isfinite(pAp)) return fail(RK_ERR_BREAKDOWN, "CG breakdown in the implicit step");
+      const double al = rr / pAp;
+      RK_CK(launch_axpby(x, al, p, 1.0, n, s));
+      RK_CK(launch_axpby(r, -al, Ap, 1.0, n, s));
+      double rr2;
+      RK_TRY(dot(r, r, &rr2));
+      RK_CK(launch_axpby(p, 1.0, r, rr2 / rr, n, s));
+      rr = rr2;
+      ++it;
+    }
+    info->iterations += it;
+    info->outer++;
+    // true residual of the step
+    RK_TRY(apply_A(x, Ap));
+    RK_CK(launch_sub(t, b, Ap, n, s));
+    double tr;
+    RK_TRY(dot(t, t, &tr));
+    info->rel_residual = std::max(info->rel_residual, std::sqrt(tr) / bn);
+    if (std::sqrt(tr) > 10.0 * o.tol * bn) return fail(RK_ERR_NOT_CONVERGED, "implicit step not converged");
+  }
+  RK_CK(launch_add(d, x, dG, n, s));
+  return RK_OK;
 }
 
 // A node is regular when its whole support (+-reach on every axis) lies in chi and
@@ -1717,6 +1868,8 @@ rk_status rk_clone(const rk_handle* parent, rk_handle** out) {
   h->err_dev = nullptr;
   h->spec32 = nullptr;
   h->spec64 = nullptr;
+  h->trans64 = nullptr;
+  h->trans32 = nullptr;
   for (int k = 0; k < 2; ++k) {
     h->tmaps32[k].clear();
     h->tmaps64[k].clear();
@@ -1924,8 +2077,12 @@ rk_status rk_get_b(rk_handle* h, double* b, void* stream) {
   return RK_OK;
 }
 
-rk_status rk_solve(rk_handle* h, const double* r, const double* g, double* d, double* u, const rk_solve_opts* opts,
-                   rk_solve_info* info, void* stream) {
+}  // extern "C"
+
+namespace {
+// rk_solve and rk_solve_neumann: Alg. 5 with optional Neumann data (q, A)
+rk_status solve_entry(rk_handle* h, const double* r, const double* g, const double* q, const double* A, double* d,
+                      double* u, const rk_solve_opts* opts, rk_solve_info* info, void* stream) {
   if (!h || !r || !d) return fail(RK_ERR_INVALID_ARG, "NULL argument");
   rk_solve_opts o;
   if (opts)
@@ -1947,7 +2104,11 @@ rk_status rk_solve(rk_handle* h, const double* r, const double* g, double* d, do
   else
     RK_TRY(stage_out_prepare(h, 2, d, bytes, &sd));
   RK_TRY(stage_out_prepare(h, 3, u, bytes, &su));
-  rk_status st = forward_solve(h, (const double*)sr.dev, (const double*)sg.dev, (double*)sd.dev, o, &inf, s);
+  Staged sq, sa;
+  RK_TRY(stage_in(h, 4, q, bytes, s, &sq));
+  RK_TRY(stage_in(h, 5, A, bytes, s, &sa));
+  rk_status st = forward_solve(h, (const double*)sr.dev, (const double*)sg.dev, (double*)sd.dev, o, &inf, s,
+                               (const double*)sq.dev, (const double*)sa.dev);
   if (st == RK_OK || st == RK_ERR_NOT_CONVERGED || st == RK_ERR_BREAKDOWN) {
     if (su.dev) RK_TRY(op_U<double>(h, (const double*)sd.dev, (double*)su.dev, s));
     RK_TRY(stage_out_finish(sd, s));
@@ -1958,6 +2119,103 @@ rk_status rk_solve(rk_handle* h, const double* r, const double* g, double* d, do
   inf.status = st;
   if (info) *info = inf;
   return st;
+}
+}  // namespace
+
+extern "C" {
+
+rk_status rk_solve(rk_handle* h, const double* r, const double* g, double* d, double* u, const rk_solve_opts* opts,
+                   rk_solve_info* info, void* stream) {
+  return solve_entry(h, r, g, nullptr, nullptr, d, u, opts, info, stream);
+}
+
+rk_status rk_solve_neumann(rk_handle* h, const double* r, const double* g, const double* q, const double* A, double* d,
+                           double* u, const rk_solve_opts* opts, rk_solve_info* info, void* stream) {
+  if (!q || !A) return fail(RK_ERR_INVALID_ARG, "NULL Neumann data");
+  return solve_entry(h, r, g, q, A, d, u, opts, info, stream);
+}
+
+rk_status rk_apply_M(rk_handle* h, const void* v, void* fm, int32_t dtype, void* stream) {
+  if (!h || !v || !fm) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  if (dtype != RK_F64 && dtype != RK_F32) return fail(RK_ERR_INVALID_ARG, "bad dtype");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * (dtype == RK_F64 ? 8 : 4);
+  Staged sv, sf;
+  RK_TRY(stage_in(h, 0, v, bytes, s, &sv));
+  RK_TRY(stage_out_prepare(h, 1, fm, bytes, &sf));
+  if (dtype == RK_F64)
+    RK_TRY(op_M<double>(h, (const double*)sv.dev, (double*)sf.dev, s));
+  else
+    RK_TRY(op_M<float>(h, (const float*)sv.dev, (float*)sf.dev, s));
+  RK_TRY(stage_out_finish(sf, s));
+  if (any_host({&sv, &sf})) RK_CK(cudaStreamSynchronize(s));
+  return RK_OK;
+}
+
+rk_status rk_lumped_mass(rk_handle* h, double* ml, void* stream) {
+  if (!h || !ml) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  Staged sm;
+  RK_TRY(stage_out_prepare(h, 1, ml, (size_t)h->nbox * 8, &sm));
+  RK_TRY(lumped_mass(h, (double*)sm.dev, s));
+  RK_TRY(stage_out_finish(sm, s));
+  if (sm.host) RK_CK(cudaStreamSynchronize(s));
+  return RK_OK;
+}
+
+rk_status rk_transient_explicit(rk_handle* h, const double* f, const double* g, double dt, int32_t n_steps, double* d,
+                                void* stream) {
+  if (!h || !f || !d || n_steps < 0 || !(dt > 0.0)) return fail(RK_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * 8;
+  Staged sf, sg, sd;
+  RK_TRY(stage_in(h, 0, f, bytes, s, &sf));
+  RK_TRY(stage_in(h, 1, g, bytes, s, &sg));
+  RK_TRY(stage_in(h, 2, d, bytes, s, &sd));
+  RK_TRY(transient_explicit(h, (const double*)sf.dev, (const double*)sg.dev, dt, n_steps, (double*)sd.dev, s));
+  RK_TRY(stage_out_finish(sd, s));
+  if (any_host({&sf, &sg, &sd})) RK_CK(cudaStreamSynchronize(s));
+  return RK_OK;
+}
+
+rk_status rk_transient_implicit(rk_handle* h, const double* f, const double* g, double dt, int32_t n_steps, double* d,
+                                const rk_solve_opts* opts, rk_solve_info* info, void* stream) {
+  if (!h || !f || !d || n_steps < 0 || !(dt > 0.0)) return fail(RK_ERR_INVALID_ARG, "bad argument");
+  rk_solve_opts o;
+  if (opts)
+    o = *opts;
+  else
+    fill_defaults(&o);
+  RK_TRY(check_opts(o));
+  rk_solve_info inf;
+  memset(&inf, 0, sizeof(inf));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * 8;
+  Staged sf, sg, sd;
+  RK_TRY(stage_in(h, 0, f, bytes, s, &sf));
+  RK_TRY(stage_in(h, 1, g, bytes, s, &sg));
+  RK_TRY(stage_in(h, 2, d, bytes, s, &sd));
+  rk_status st = transient_implicit(h, (const double*)sf.dev, (const double*)sg.dev, dt, n_steps, (double*)sd.dev, o,
+                                    &inf, s);
+  if (st == RK_OK) RK_TRY(stage_out_finish(sd, s));
+  RK_CK(cudaStreamSynchronize(s));
+  inf.status = st;
+  if (info) *info = inf;
+  return st;
+}
+
+rk_status rk_boundary_rhs(rk_handle* h, const double* q, const double* A, double* fq, void* stream) {
+  if (!h || !q || !A || !fq) return fail(RK_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * 8;
+  Staged sq, sa, sf;
+  RK_TRY(stage_in(h, 0, q, bytes, s, &sq));
+  RK_TRY(stage_in(h, 1, A, bytes, s, &sa));
+  RK_TRY(stage_out_prepare(h, 2, fq, bytes, &sf));
+  RK_TRY(boundary_rhs(h, (const double*)sq.dev, (const double*)sa.dev, (double*)sf.dev, s));
+  RK_TRY(stage_out_finish(sf, s));
+  if (any_host({&sq, &sa, &sf})) RK_CK(cudaStreamSynchronize(s));
+  return RK_OK;
 }
 
 rk_status rk_solve_adjoint(rk_handle* h, const double* r, const double* g, const double* u_target, double* dJ_dr,

@@ -142,6 +142,11 @@ cudaError_t launch_sub(double* out, const double* a, const double* b, long long 
 cudaError_t launch_mul(double* a, const double* b, long long n, cudaStream_t s);
 // u8 -> double
 cudaError_t launch_u8_to_f64(double* out, const uint8_t* m, long long n, cudaStream_t s);
+// y = a x + b y
+cudaError_t launch_axpby(double* y, double a, const double* x, double b, long long n, cudaStream_t s);
+// d += dt (f - Kd) / ml where mask (forward Euler with lumped mass)
+cudaError_t launch_explicit_step(double* d, const double* f, const double* Kd, const double* ml, const uint8_t* mask,
+                                 double dt, long long n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fill(T* p, T v, long long n, cudaStream_t s);
 template <typename T>

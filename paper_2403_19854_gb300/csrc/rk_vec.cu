@@ -513,6 +513,29 @@ cudaError_t launch_add(double* d, const double* a, const double* b, long long n,
   return cudaGetLastError();
 }
 
+// y = a x + b y
+__global__ void k_axpby(double* y, double a, const double* x, double b, long long n) {
+  RK_GRID_LOOP(i, n) y[i] = a * x[i] + b * y[i];
+}
+cudaError_t launch_axpby(double* y, double a, const double* x, double b, long long n, cudaStream_t s) {
+  count_launch();
+  k_axpby<<<ew_grid(n), 256, 0, s>>>(y, a, x, b, n);
+  return cudaGetLastError();
+}
+
+// forward Euler with lumped mass on the free nodes (Alg. C.3):
+// d += dt (f - K d) / M^l where mask, d untouched elsewhere
+__global__ void k_explicit_step(double* d, const double* f, const double* Kd, const double* ml, const uint8_t* mask,
+                                double dt, long long n) {
+  RK_GRID_LOOP(i, n) if (mask[i]) d[i] += dt * (f[i] - Kd[i]) / ml[i];
+}
+cudaError_t launch_explicit_step(double* d, const double* f, const double* Kd, const double* ml, const uint8_t* mask,
+                                 double dt, long long n, cudaStream_t s) {
+  count_launch();
+  k_explicit_step<<<ew_grid(n), 256, 0, s>>>(d, f, Kd, ml, mask, dt, n);
+  return cudaGetLastError();
+}
+
 __global__ void k_sub(double* d, const double* a, const double* b, long long n) {
   RK_GRID_LOOP(i, n) d[i] = a[i] - b[i];
 }

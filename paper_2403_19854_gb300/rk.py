@@ -27,7 +27,8 @@ EXPORTED = ["rk_default_solve_opts", "rk_supported_length", "rk_setup", "rk_sing
             "rk_rhs", "rk_eval_u", "rk_eval_u_transpose", "rk_get_b", "rk_get_shape", "rk_solve",
             "rk_solve_adjoint", "rk_destroy", "rk_status_string", "rk_last_error_message",
             "rk_kernel_launches", "rk_profile_enable", "rk_profile_read", "rk_profile_class_name",
-            "rk_solve_vjp", "rk_clone", "rk_solve_batched", "rk_apply_precond"]
+            "rk_solve_vjp", "rk_clone", "rk_solve_batched", "rk_apply_precond", "rk_boundary_rhs",
+            "rk_solve_neumann", "rk_apply_M", "rk_lumped_mass", "rk_transient_explicit", "rk_transient_implicit"]
 PROF_CLASSES = 12
 
 
@@ -80,6 +81,14 @@ def lib():
     L.rk_singular_nodes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.rk_apply_K.argtypes = [vp, vp, vp, i32, vp]
     L.rk_apply_precond.argtypes = [vp, vp, vp, i32, vp]
+    L.rk_boundary_rhs.argtypes = [vp, vp, vp, vp, vp]
+    L.rk_apply_M.argtypes = [vp, vp, vp, i32, vp]
+    L.rk_lumped_mass.argtypes = [vp, vp, vp]
+    L.rk_transient_explicit.argtypes = [vp, vp, vp, ctypes.c_double, i32, vp, vp]
+    L.rk_transient_implicit.argtypes = [vp, vp, vp, ctypes.c_double, i32, vp, ctypes.POINTER(SolveOpts),
+                                        ctypes.POINTER(SolveInfo), vp]
+    L.rk_solve_neumann.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo),
+                                   vp]
     for name in ("rk_rhs", "rk_eval_u", "rk_eval_u_transpose"):
         getattr(L, name).argtypes = [vp, vp, vp, vp]
     L.rk_get_b.argtypes = [vp, vp, vp]
@@ -310,8 +319,61 @@ class Handle:
         return out
 
     # ------------------------------------------------------------------ solves
-    def solve(self, r, g=None, d=None, u=None, opts=None, want_u=True, stream=None, raise_on_error=True, **kw):
-        """Alg. 5: returns (d, u, info dict)."""
+    # ------------------------------------------------------- time-dependent
+    def apply_M(self, v, out=None, stream=None):
+        """f^m = M v (Alg. C.1); float32 -> FP32 path, float64 -> FP64."""
+        is32 = (str(v.dtype).endswith("float32"))
+        dt = RK_F32 if is32 else RK_F64
+        if out is None:
+            out = _like(v, dt, self.nbox)
+        pv, kv = _ptr(v)
+        po, ko = _ptr(out)
+        _check(lib().rk_apply_M(self._h, pv, po, dt, stream if stream is not None else _stream(v)))
+        return out
+
+    def lumped_mass(self, out=None, like=None, stream=None):
+        """M^l (Alg. C.2), FP64."""
+        if out is None:
+            out = _like(like if like is not None else np.empty(1), RK_F64, self.nbox)
+        po, ko = _ptr(out)
+        _check(lib().rk_lumped_mass(self._h, po, stream if stream is not None else _stream(out)))
+        return out
+
+    def transient_explicit(self, f, g, dt, n_steps, d, stream=None):
+        """Alg. C.3 (forward Euler, lumped mass): advances d in place by n_steps."""
+        pf, kf = _ptr(f)
+        pg, kg = _ptr(g)
+        pd, kd = _ptr(d)
+        _check(lib().rk_transient_explicit(self._h, pf, pg, float(dt), int(n_steps), pd,
+                                           stream if stream is not None else _stream(d)))
+        return d
+
+    def transient_implicit(self, f, g, dt, n_steps, d, opts=None, stream=None, **kw):
+        """Alg. C.4 (backward Euler, FP64 CG per step): advances d in place; returns info."""
+        if opts is None:
+            opts = default_opts(**kw)
+        info = SolveInfo()
+        pf, kf = _ptr(f)
+        pg, kg = _ptr(g)
+        pd, kd = _ptr(d)
+        _check(lib().rk_transient_implicit(self._h, pf, pg, float(dt), int(n_steps), pd, ctypes.byref(opts),
+                                           ctypes.byref(info), stream if stream is not None else _stream(d)))
+        return info.as_dict()
+
+    def boundary_rhs(self, q, A, out=None, stream=None):
+        """f^q of Alg. A.1 for Neumann data q and boundary weights A (FP64)."""
+        if out is None:
+            out = _like(q, RK_F64, self.nbox)
+        pq, kq = _ptr(q)
+        pa, ka = _ptr(A)
+        po, ko = _ptr(out)
+        _check(lib().rk_boundary_rhs(self._h, pq, pa, po, stream if stream is not None else _stream(q)))
+        return out
+
+    def solve(self, r, g=None, d=None, u=None, opts=None, want_u=True, stream=None, raise_on_error=True, q=None,
+              A=None, **kw):
+        """Alg. 5: returns (d, u, info dict); with q and A the Neumann term f^q of
+        Alg. A.1 joins the right-hand side."""
         if opts is None:
             opts = default_opts(**kw)
         if d is None:
@@ -323,8 +385,14 @@ class Handle:
         pg, kg = _ptr(g)
         pd, kd = _ptr(d)
         pu, ku = _ptr(u)
-        st = lib().rk_solve(self._h, pr, pg, pd, pu, ctypes.byref(opts), ctypes.byref(info),
-                            stream if stream is not None else _stream(r))
+        if q is not None:
+            pq, kq = _ptr(q)
+            pa, ka = _ptr(A)
+            st = lib().rk_solve_neumann(self._h, pr, pg, pq, pa, pd, pu, ctypes.byref(opts), ctypes.byref(info),
+                                        stream if stream is not None else _stream(r))
+        else:
+            st = lib().rk_solve(self._h, pr, pg, pd, pu, ctypes.byref(opts), ctypes.byref(info),
+                                stream if stream is not None else _stream(r))
         if raise_on_error:
             _check(st)
         return d, u, info.as_dict()

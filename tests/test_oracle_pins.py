@@ -373,3 +373,46 @@ def test_singular_moment_is_detected():
     chi[3 + 8 * (3 + 8 * 3)] = 1
     o = Oracle((8, 8, 8), (0.1, 0.1, 0.1), 2.0, 1, chi)
     assert o.nsingular == 1 and o.first_singular == 3 + 8 * (3 + 8 * 3)
+
+
+def test_boundary_integral_moments_alg_a1():
+    """f^q of Alg. A.1 (Eq. A.2): f^q_I = sum_S Psi_I(x_S) q_S A_S.  Partition of
+    unity and linear reproduction of Psi fix its zeroth and first moments:
+    sum_I f^q_I = sum_S q_S A_S and sum_I f^q_I x_I = sum_S q_S A_S x_S."""
+    p = W.cube_problem(12, 2.5, 1, "zero")
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    rng = np.random.default_rng(7)
+    gam = p.chi_gamma > 0
+    A = np.where(gam, p.h[0] ** 2 * rng.uniform(0.5, 1.0, p.nbox), 0.0)
+    q = np.where(gam, rng.standard_normal(p.nbox), 0.0)
+    fq = o.eval_u_transpose(q * A)
+    X, Y, Z = p.coords()
+    tot = np.sum(q * A)
+    assert abs(fq.sum() - tot) <= 1e-12 * np.sum(np.abs(q * A))
+    for c in (X, Y, Z):
+        assert abs(np.sum(fq * c) - np.sum(q * A * c)) <= 1e-12 * np.sum(np.abs(q * A))
+    assert np.all(fq[p.chi == 0] == 0)
+
+
+def test_mass_terms_appendix_c():
+    """M = sum_S V_S Psi(x_S) Psi(x_S)^T (Eq. C.5, DNI) applied as U^T (V o U v):
+    symmetric; the lumped mass (row sums, Eq. C.9) equals U^T V by partition of
+    unity and sums to the volume; a linear field v_I = x_I gives sum_I (Mv)_I =
+    sum_S V_S x_S (linear reproduction)."""
+    p = W.cube_problem(12, 2.5, 1, "zero")
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    m = p.chi > 0
+
+    def M(v):
+        return o.eval_u_transpose(p.V * o.eval_u(v))
+
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(p.nbox) * m
+    y = rng.standard_normal(p.nbox) * m
+    assert abs(np.dot(y, M(x)) - np.dot(x, M(y))) <= 1e-13 * abs(np.dot(x, M(x)))
+    assert np.dot(x, M(x)) > 0
+    ml = o.eval_u_transpose(p.V)
+    assert np.allclose(M(m.astype(float)), ml, rtol=0, atol=1e-14 * ml.max())
+    assert abs(ml.sum() - p.V.sum()) <= 1e-13 * p.V.sum()
+    X, _, _ = p.coords()
+    assert abs(M(X * m).sum() - np.sum(p.V * X)) <= 1e-13 * np.sum(np.abs(p.V * X))
