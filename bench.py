@@ -328,6 +328,35 @@ def run_ours(args):
         cufft[dt_name] = {"ms_fft_only_per_Ku": c0.elapsed_time(c1) / reps, "real_3d_ffts_per_Ku": 10}
         del f
 
+    # the operators of Appendices A and C at the same size (one launch sequence each)
+    appendix = {}
+    Ha = rk.Handle(p.n, p.h, chi, cg, V, 1, 2.5)
+    qa = torch.rand(p.nbox, dtype=torch.float64, device=dev) * cg
+    Aw = cg.double() * (p.h[0] ** 2)
+    v64 = torch.rand(p.nbox, dtype=torch.float64, device=dev) * chi
+    f_out = torch.empty_like(v64)
+    v32 = v64.float()
+    f32 = torch.empty_like(v32)
+    dd = v64.clone()
+
+    def timed(fn, reps):
+        fn()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / reps
+
+    appendix["boundary_rhs_f64_ms"] = timed(lambda: Ha.boundary_rhs(qa, Aw, out=f_out), 3)
+    appendix["apply_M_f64_ms"] = timed(lambda: Ha.apply_M(v64, out=f_out), 3)
+    appendix["apply_M_f32_ms"] = timed(lambda: Ha.apply_M(v32, out=f32), 10)
+    appendix["lumped_mass_f64_ms"] = timed(lambda: Ha.lumped_mass(out=f_out), 3)
+    appendix["explicit_step_f64_ms"] = timed(lambda: Ha.transient_explicit(f_out, g, 1e-9, 1, dd), 3)
+    Ha.close()
+    del qa, Aw, v64, f_out, v32, f32, dd
+
     # isolated K.u rates (resident d, f)
     H = rk.Handle(p.n, p.h, chi, cg, V, 1, 2.5)
     kd = {}
@@ -434,6 +463,7 @@ def run_ours(args):
             "fp64_solve": fp64,
             "kU_isolated": kd,
             "cufft_comparison": cufft,
+            "appendix_ops": appendix,
             "profiled_step_ms": profiled_ms,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
