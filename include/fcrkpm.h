@@ -254,6 +254,24 @@ rk_status rk_transient_implicit(rk_handle* h, const double* f, const double* g, 
                                 const rk_solve_opts* opts, rk_solve_info* info, void* stream);
 
 /*
+ * Nonlinear reaction terms (Appendix B, the scalar form of Eq. B.1-B.4 and B.9):
+ *   f^N = chi o F^{-1}[ sum_p F(chi V b0_p N(u^h)) F(Hbar^a_p) ],  u^h from Alg. 3,
+ * with a built-in pointwise nonlinearity N (rk_nonlinearity; c >= 0 makes N
+ * nondecreasing): RK_NL_CUBIC c u^3, RK_NL_SINH c sinh(u), RK_NL_EXP c exp(u).
+ * rk_nonlinear_force -- f^N(d) (Alg. B.2 of the paper's listing for Eq. B.9).
+ * rk_solve_nonlinear -- Alg. B.3: K d + f^N(d) = f^r on the free nodes, d = g on
+ *   Gamma_g, by nonlinear CG (Polak-Ribiere+, exact line search by Newton's method
+ *   on the convex energy), FP64, from d = d_Gamma, until |R| <= opts->tol |R_0|
+ *   (opts->max_iter iterations at most; precision and the mixed options are not
+ *   used).  u may be NULL.  info: iterations, relative residual, operator
+ *   applications.  Errors: RK_ERR_NOT_CONVERGED, RK_ERR_BREAKDOWN (line search).
+ */
+typedef enum rk_nonlinearity { RK_NL_CUBIC = 0, RK_NL_SINH = 1, RK_NL_EXP = 2 } rk_nonlinearity;
+rk_status rk_nonlinear_force(rk_handle* h, const double* d, int32_t kind, double c, double* fN, void* stream);
+rk_status rk_solve_nonlinear(rk_handle* h, const double* r, const double* g, int32_t kind, double c, double* d,
+                             double* u, const rk_solve_opts* opts, rk_solve_info* info, void* stream);
+
+/*
  * rk_solve_adjoint -- gradient of J = 1/2 sum_{chi} (u^h - u_target)^2 with respect
  * to the source r and the Dirichlet data g, for the solve of rk_solve.  The forward
  * solve is recomputed from (r, g) (nothing is kept between calls); one adjoint

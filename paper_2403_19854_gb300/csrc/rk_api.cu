@@ -167,9 +167,11 @@ struct rk_handle {
   SymbolArgs<double> sym64;
   float* mult32 = nullptr;   // z SYM multiplier tables (owned by the set-up handle)
   double* mult64 = nullptr;
-  // transient solvers (Appendix C): 5 FP64 and 1 FP32 scratch fields, on first use
+  // transient and nonlinear solvers (Appendices B, C): 5 FP64 and 1 FP32 scratch
+  // fields and 2 x 608 reduction partials, on first use
   double* trans64 = nullptr;
   float* trans32 = nullptr;
+  double* part2 = nullptr;
   // staging of host arrays
   double* stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   unsigned long long* counters = nullptr;  // singular count, first singular
@@ -1304,6 +1306,7 @@ float* trans_scratch<float>(rk_handle* h) { return h->trans32; }
 rk_status ensure_transient(rk_handle* h) {
   if (!h->trans64) RK_TRY(h->alloc(&h->trans64, (size_t)5 * h->nbox));
   if (!h->trans32) RK_TRY(h->alloc(&h->trans32, (size_t)h->nbox));
+  if (!h->part2) RK_TRY(h->alloc(&h->part2, (size_t)2 * kRedBlocks));
   return RK_OK;
 }
 
@@ -1424,6 +1427,122 @@ rk_status transient_implicit(rk_handle* h, const double* f, const double* g, dou
     if (std::sqrt(tr) > 10.0 * o.tol * bn) return fail(RK_ERR_NOT_CONVERGED, "implicit step not converged");
   }
   RK_CK(launch_add(d, x, dG, n, s));
+  return RK_OK;
+}
+
+// ------------------------------------------------- nonlinear reaction terms
+// Appendix B: f^N = chi o F^{-1}[sum_p F(chi V b0_p N_u) F(Hbar^a_p)] with
+// N_u = N(u^h), u^h from Alg. 3 (Eq. B.4, B.9): the chain of Alg. 3, the
+// pointwise nonlinearity, the chain of Alg. 4.
+rk_status nonlinear_force(rk_handle* h, const double* d, int kind, double c, double* fN, cudaStream_t s) {
+  RK_TRY(ensure_transient(h));
+  double* u = h->trans64;
+  double* Nu = h->trans64 + (size_t)1 * h->nbox;
+  RK_TRY(op_U<double>(h, d, u, s));
+  RK_CK(launch_nl_apply(Nu, u, h->chi, kind, c, h->nbox, s));
+  return op_UT<double>(h, Nu, fN, h->chiV64, nullptr, s);
+}
+
+// Alg. B.3: K d + f^N(d) = f^r on the free nodes, d = g on Gamma_g, by nonlinear
+// CG (Polak-Ribiere+) on the convex energy E = 1/2 d.K d + sum_S V_S F(u_S) - d.f^r
+// (F' = N, nondecreasing).  The line search along p is Newton's method on
+// phi'(alpha) = p.(K x - f^r) + alpha p.K p + sum_S V_S w_S N(u_S + alpha w_S),
+// w = U p: after one K.p and one U.p per direction it needs only node sums.
+rk_status solve_nonlinear(rk_handle* h, const double* r, const double* g, int kind, double c, double* d,
+                          const rk_solve_opts& o, rk_solve_info* info, cudaStream_t s) {
+  RK_TRY(ensure_solver(h));
+  RK_TRY(ensure_transient(h));
+  const long long n = h->nbox;
+  double* x = h->v64(0);    // free part of d
+  double* R = h->v64(1);    // gradient (residual) on chi_Omega
+  double* p = h->v64(2);
+  double* Kp = h->v64(3);
+  double* F = h->v64(4);    // chi_Omega o f^r
+  double* dG = h->v64(5);
+  double* Kx = h->v64(6);   // chi_Omega o K (x + d_Gamma)
+  double* Rn = h->v64(8);
+  double* u = h->trans64 + (size_t)2 * n;  // u^h(x + d_Gamma)
+  double* w = h->trans64 + (size_t)3 * n;  // U p
+  double* fN = h->trans64 + (size_t)4 * n;
+  auto dot = [&](const double* a, const double* b2, double* out) -> rk_status {
+    RK_CK(launch_dot<double, double>(a, b2, n, h->partials, h->dscal, s));
+    return read_scalar(h, h->dscal, out, s);
+  };
+  auto line = [&](double alpha, double* s0, double* s1) -> rk_status {
+    RK_CK(launch_nl_line(u, w, h->V, h->chi, kind, c, alpha, n, h->part2, h->dscal, s));
+    RK_CK(cudaMemcpyAsync(h->hscal, h->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RK_CK(cudaStreamSynchronize(s));
+    *s0 = h->hscal[0];
+    *s1 = h->hscal[1];
+    return RK_OK;
+  };
+  // gradient R = chi_Omega o (K x + f^N - f^r) at the current u
+  auto gradient = [&](double* out) -> rk_status {
+    double* Nu = h->trans64 + (size_t)1 * n;
+    RK_CK(launch_nl_apply(Nu, u, h->chi, kind, c, n, s));
+    RK_TRY(op_UT<double>(h, Nu, fN, h->chiV64, nullptr, s));
+    RK_CK(launch_add(out, Kx, fN, n, s));
+    RK_CK(launch_sub(out, out, F, n, s));
+    RK_CK(launch_mask(out, out, h->chi_omega, n, s));
+    return RK_OK;
+  };
+  if (g)
+    RK_CK(launch_dirichlet_d0(dG, g, h->chi_gamma, n, s));
+  else
+    RK_CK(launch_fill<double>(dG, 0.0, n, s));
+  RK_TRY(op_UT<double>(h, r, F, h->chiV64, nullptr, s));
+  RK_CK(launch_mask(F, F, h->chi_omega, n, s));
+  RK_CK(launch_fill<double>(x, 0.0, n, s));
+  RK_TRY(op_U<double>(h, dG, u, s));
+  RK_TRY(op_K<double>(h, dG, Kx, h->chi, h->chi_omega, s));
+  info->matvec_f64 += 1;
+  RK_TRY(gradient(R));
+  double rr0, rr;
+  RK_TRY(dot(R, R, &rr0));
+  rr = rr0;
+  info->f_norm = std::sqrt(rr0);
+  const double target = o.tol * std::sqrt(rr0);
+  RK_CK(launch_axpby(p, -1.0, R, 0.0, n, s));
+  int it = 0;
+  while (std::sqrt(rr) > target && it < o.max_iter) {
+    RK_TRY(op_K<double>(h, p, Kp, h->chi_omega, h->chi_omega, s));
+    RK_TRY(op_U<double>(h, p, w, s));
+    info->matvec_f64 += 1;
+    double pKp, pKx, pF;
+    RK_TRY(dot(p, Kp, &pKp));
+    RK_TRY(dot(p, Kx, &pKx));
+    RK_TRY(dot(p, F, &pF));
+    const double c0 = pKx - pF;
+    double alpha = 0.0;
+    for (int k = 0; k < 40; ++k) {
+      double s0, s1;
+      RK_TRY(line(alpha, &s0, &s1));
+      const double d1 = c0 + alpha * pKp + s0, d2 = pKp + s1;
+      if (!(d2 > 0.0) || !std::isfinite(d1)) return fail(RK_ERR_BREAKDOWN, "nonlinear CG: line search failed");
+      const double step = d1 / d2;
+      alpha -= step;
+      if (std::abs(step) <= 1e-15 * std::max(std::abs(alpha), 1e-300)) break;
+    }
+    RK_CK(launch_axpby(x, alpha, p, 1.0, n, s));
+    RK_CK(launch_axpby(u, alpha, w, 1.0, n, s));
+    RK_CK(launch_axpby(Kx, alpha, Kp, 1.0, n, s));
+    RK_TRY(gradient(Rn));
+    double rn_rn, rn_r;
+    RK_TRY(dot(Rn, Rn, &rn_rn));
+    RK_TRY(dot(Rn, R, &rn_r));
+    const double beta = std::max(0.0, (rn_rn - rn_r) / rr);  // Polak-Ribiere+
+    RK_CK(launch_axpby(p, -1.0, Rn, beta, n, s));
+    double slope;
+    RK_TRY(dot(p, Rn, &slope));
+    if (!(slope < 0.0)) RK_CK(launch_axpby(p, -1.0, Rn, 0.0, n, s));  // not a descent direction: restart
+    RK_CK(launch_copy<double>(R, Rn, n, s));
+    rr = rn_rn;
+    ++it;
+  }
+  info->iterations = it;
+  info->rel_residual = rr0 > 0.0 ? std::sqrt(rr / rr0) : 0.0;
+  RK_CK(launch_add(d, x, dG, n, s));
+  if (std::sqrt(rr) > target) return fail(RK_ERR_NOT_CONVERGED, "nonlinear CG: tolerance not reached");
   return RK_OK;
 }
 
@@ -1870,6 +1989,7 @@ rk_status rk_clone(const rk_handle* parent, rk_handle** out) {
   h->spec64 = nullptr;
   h->trans64 = nullptr;
   h->trans32 = nullptr;
+  h->part2 = nullptr;
   for (int k = 0; k < 2; ++k) {
     h->tmaps32[k].clear();
     h->tmaps64[k].clear();
@@ -2199,6 +2319,52 @@ rk_status rk_transient_implicit(rk_handle* h, const double* f, const double* g, 
                                     &inf, s);
   if (st == RK_OK) RK_TRY(stage_out_finish(sd, s));
   RK_CK(cudaStreamSynchronize(s));
+  inf.status = st;
+  if (info) *info = inf;
+  return st;
+}
+
+rk_status rk_nonlinear_force(rk_handle* h, const double* d, int32_t kind, double c, double* fN, void* stream) {
+  if (!h || !d || !fN || kind < RK_NL_CUBIC || kind > RK_NL_EXP) return fail(RK_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * 8;
+  Staged sd, sf;
+  RK_TRY(stage_in(h, 0, d, bytes, s, &sd));
+  RK_TRY(stage_out_prepare(h, 1, fN, bytes, &sf));
+  RK_TRY(nonlinear_force(h, (const double*)sd.dev, kind, c, (double*)sf.dev, s));
+  RK_TRY(stage_out_finish(sf, s));
+  if (any_host({&sd, &sf})) RK_CK(cudaStreamSynchronize(s));
+  return RK_OK;
+}
+
+rk_status rk_solve_nonlinear(rk_handle* h, const double* r, const double* g, int32_t kind, double c, double* d,
+                             double* u, const rk_solve_opts* opts, rk_solve_info* info, void* stream) {
+  if (!h || !r || !d || kind < RK_NL_CUBIC || kind > RK_NL_EXP || !(c >= 0.0))
+    return fail(RK_ERR_INVALID_ARG, "bad argument");
+  rk_solve_opts o;
+  if (opts)
+    o = *opts;
+  else
+    fill_defaults(&o);
+  RK_TRY(check_opts(o));
+  rk_solve_info inf;
+  memset(&inf, 0, sizeof(inf));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * 8;
+  auto t0 = std::chrono::steady_clock::now();
+  Staged sr, sg, sd, su;
+  RK_TRY(stage_in(h, 0, r, bytes, s, &sr));
+  RK_TRY(stage_in(h, 1, g, bytes, s, &sg));
+  RK_TRY(stage_out_prepare(h, 2, d, bytes, &sd));
+  RK_TRY(stage_out_prepare(h, 3, u, bytes, &su));
+  rk_status st = solve_nonlinear(h, (const double*)sr.dev, (const double*)sg.dev, kind, c, (double*)sd.dev, o, &inf, s);
+  if (st == RK_OK || st == RK_ERR_NOT_CONVERGED) {
+    if (su.dev) RK_TRY(op_U<double>(h, (const double*)sd.dev, (double*)su.dev, s));
+    RK_TRY(stage_out_finish(sd, s));
+    RK_TRY(stage_out_finish(su, s));
+  }
+  RK_CK(cudaStreamSynchronize(s));
+  inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   inf.status = st;
   if (info) *info = inf;
   return st;

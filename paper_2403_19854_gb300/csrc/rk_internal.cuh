@@ -142,6 +142,12 @@ cudaError_t launch_sub(double* out, const double* a, const double* b, long long 
 cudaError_t launch_mul(double* a, const double* b, long long n, cudaStream_t s);
 // u8 -> double
 cudaError_t launch_u8_to_f64(double* out, const uint8_t* m, long long n, cudaStream_t s);
+// nonlinear reaction terms (kind 0: c u^3, 1: c sinh u, 2: c exp u)
+cudaError_t launch_nl_apply(double* Nu, const double* u, const uint8_t* chi, int kind, double c, long long n,
+                            cudaStream_t s);
+// out2 = {sum_chi V w N(u + alpha w), sum_chi V w^2 N'(u + alpha w)}; partials2 holds 2 x kRedBlocks
+cudaError_t launch_nl_line(const double* u, const double* w, const double* V, const uint8_t* chi, int kind, double c,
+                           double alpha, long long n, double* partials2, double* out2, cudaStream_t s);
 // y = a x + b y
 cudaError_t launch_axpby(double* y, double a, const double* x, double b, long long n, cudaStream_t s);
 // d += dt (f - Kd) / ml where mask (forward Euler with lumped mass)

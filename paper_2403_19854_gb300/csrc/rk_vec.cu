@@ -379,6 +379,73 @@ cudaError_t launch_cg_set_rr(const double* partials, CGState* st, cudaStream_t s
   return cudaGetLastError();
 }
 
+// ------------------------------------------------- nonlinear reaction terms
+// N(u) and N'(u) of the built-in reaction nonlinearities (Appendix B, Eq. B.1)
+__device__ __forceinline__ double nl_value(int kind, double c, double u) {
+  switch (kind) {
+    case 0: return c * u * u * u;  // cubic
+    case 1: return c * sinh(u);
+    case 2: return c * exp(u);
+    default: return 0.0;
+  }
+}
+__device__ __forceinline__ double nl_slope(int kind, double c, double u) {
+  switch (kind) {
+    case 0: return 3.0 * c * u * u;
+    case 1: return c * cosh(u);
+    case 2: return c * exp(u);
+    default: return 0.0;
+  }
+}
+
+// Nu = chi ? N(u) : 0
+__global__ void k_nl_apply(double* Nu, const double* u, const uint8_t* chi, int kind, double c, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    Nu[i] = chi[i] ? nl_value(kind, c, u[i]) : 0.0;
+}
+cudaError_t launch_nl_apply(double* Nu, const double* u, const uint8_t* chi, int kind, double c, long long n,
+                            cudaStream_t s) {
+  count_launch();
+  k_nl_apply<<<kRedBlocks, kRedThreads, 0, s>>>(Nu, u, chi, kind, c, n);
+  return cudaGetLastError();
+}
+
+// Line search sums over chi: out[0] = sum V w N(u + alpha w), out[1] = sum V w^2 N'(u + alpha w)
+// (fixed grid and order: reproducible)
+__global__ void __launch_bounds__(kRedThreads) k_nl_line(const double* u, const double* w, const double* V,
+                                                        const uint8_t* chi, int kind, double c, double alpha,
+                                                        long long n, double* part) {
+  double s0 = 0.0, s1 = 0.0;
+  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads)
+    if (chi[i]) {
+      const double wi = w[i], ui = u[i] + alpha * wi, vw = V[i] * wi;
+      s0 += vw * nl_value(kind, c, ui);
+      s1 += vw * wi * nl_slope(kind, c, ui);
+    }
+  s0 = block_sum(s0);
+  s1 = block_sum(s1);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0;
+    part[kRedBlocks + blockIdx.x] = s1;
+  }
+}
+__global__ void __launch_bounds__(kRedThreads) k_reduce2_to(const double* part, double* out) {
+  const double a = reduce_partials(part);
+  const double b = reduce_partials(part + kRedBlocks);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+  }
+}
+cudaError_t launch_nl_line(const double* u, const double* w, const double* V, const uint8_t* chi, int kind, double c,
+                           double alpha, long long n, double* partials2, double* out2, cudaStream_t s) {
+  count_launch();
+  k_nl_line<<<kRedBlocks, kRedThreads, 0, s>>>(u, w, V, chi, kind, c, alpha, n, partials2);
+  count_launch();
+  k_reduce2_to<<<1, kRedThreads, 0, s>>>(partials2, out2);
+  return cudaGetLastError();
+}
+
 // 16-byte vectors of T (4 floats / 2 doubles)
 template <typename T>
 struct Vec16 {

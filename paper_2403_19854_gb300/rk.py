@@ -28,7 +28,9 @@ EXPORTED = ["rk_default_solve_opts", "rk_supported_length", "rk_setup", "rk_sing
             "rk_solve_adjoint", "rk_destroy", "rk_status_string", "rk_last_error_message",
             "rk_kernel_launches", "rk_profile_enable", "rk_profile_read", "rk_profile_class_name",
             "rk_solve_vjp", "rk_clone", "rk_solve_batched", "rk_apply_precond", "rk_boundary_rhs",
-            "rk_solve_neumann", "rk_apply_M", "rk_lumped_mass", "rk_transient_explicit", "rk_transient_implicit"]
+            "rk_solve_neumann", "rk_apply_M", "rk_lumped_mass", "rk_transient_explicit", "rk_transient_implicit",
+            "rk_nonlinear_force", "rk_solve_nonlinear"]
+NONLINEARITIES = {"cubic": 0, "sinh": 1, "exp": 2}
 PROF_CLASSES = 12
 
 
@@ -83,6 +85,9 @@ def lib():
     L.rk_apply_precond.argtypes = [vp, vp, vp, i32, vp]
     L.rk_boundary_rhs.argtypes = [vp, vp, vp, vp, vp]
     L.rk_apply_M.argtypes = [vp, vp, vp, i32, vp]
+    L.rk_nonlinear_force.argtypes = [vp, vp, i32, ctypes.c_double, vp, vp]
+    L.rk_solve_nonlinear.argtypes = [vp, vp, vp, i32, ctypes.c_double, vp, vp, ctypes.POINTER(SolveOpts),
+                                     ctypes.POINTER(SolveInfo), vp]
     L.rk_lumped_mass.argtypes = [vp, vp, vp]
     L.rk_transient_explicit.argtypes = [vp, vp, vp, ctypes.c_double, i32, vp, vp]
     L.rk_transient_implicit.argtypes = [vp, vp, vp, ctypes.c_double, i32, vp, ctypes.POINTER(SolveOpts),
@@ -359,6 +364,36 @@ class Handle:
         _check(lib().rk_transient_implicit(self._h, pf, pg, float(dt), int(n_steps), pd, ctypes.byref(opts),
                                            ctypes.byref(info), stream if stream is not None else _stream(d)))
         return info.as_dict()
+
+    # ------------------------------------------------------------ nonlinear
+    def nonlinear_force(self, d, kind, c, out=None, stream=None):
+        """f^N(d) of Appendix B for N in NONLINEARITIES ("cubic", "sinh", "exp") times c."""
+        if out is None:
+            out = _like(d, RK_F64, self.nbox)
+        pd, kd = _ptr(d)
+        po, ko = _ptr(out)
+        _check(lib().rk_nonlinear_force(self._h, pd, NONLINEARITIES[kind], float(c), po,
+                                        stream if stream is not None else _stream(d)))
+        return out
+
+    def solve_nonlinear(self, r, g, kind, c, d=None, u=None, opts=None, stream=None, raise_on_error=True, **kw):
+        """Alg. B.3 (nonlinear CG): returns (d, u, info dict)."""
+        if opts is None:
+            opts = default_opts(**kw)
+        if d is None:
+            d = _like(r, RK_F64, self.nbox)
+        if u is None:
+            u = _like(r, RK_F64, self.nbox)
+        info = SolveInfo()
+        pr, kr = _ptr(r)
+        pg, kg = _ptr(g)
+        pd, kd = _ptr(d)
+        pu, ku = _ptr(u)
+        st = lib().rk_solve_nonlinear(self._h, pr, pg, NONLINEARITIES[kind], float(c), pd, pu, ctypes.byref(opts),
+                                      ctypes.byref(info), stream if stream is not None else _stream(r))
+        if raise_on_error:
+            _check(st)
+        return d, u, info.as_dict()
 
     def boundary_rhs(self, q, A, out=None, stream=None):
         """f^q of Alg. A.1 for Neumann data q and boundary weights A (FP64)."""
