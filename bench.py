@@ -183,14 +183,19 @@ def pass_bytes(cls, w, s=4):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # kernels that can dominate a step, from one ncu capture of the 256^3-box cube
-# K.u (profiles/dram_Ku_f32_cube256.md).  A value holds only while the source
-# files of the kernel are unchanged: the sha256 of each is checked at run time
-# and the traffic is reported as null otherwise.
+# K.u (profiles/dram_Ku_f32_cube256.md).  A value holds only while the kernel is
+# unchanged: the sha256 of each listed source region (the kernel and its
+# argument struct) is checked at run time, and the traffic is null otherwise.
 MEASURED_TRAFFIC = {
-    ("stiff_pointwise", "f32", 256): (384381952 + 212011264, {
-        "paper_2403_19854_gb300/csrc/rk_vec.cu": "9754bd819b869626448bc2b56587922f2a669e4e4e3867f1143259a183a2db1a",
-        "paper_2403_19854_gb300/csrc/rk_internal.cuh": "4cd20500eb91c2aef84798da35a8ddded01366fe37a6c4fe3b091855b3867626",
-    }),
+    ("stiff_pointwise", "f32", 256): (384381952 + 212011264, [
+        ("paper_2403_19854_gb300/csrc/rk_vec.cu",
+         "template <typename T, int S>\n__global__ void __launch_bounds__(256) k_pointwise_stiff",
+         "template cudaError_t launch_pointwise_stiff<double>",
+         "e3a2afd194e7caac07baa29bfcad4eed42c24ba9188ce74e060d805fa6b6e4a8"),
+        ("paper_2403_19854_gb300/csrc/rk_internal.cuh", "struct PointwiseArgs {",
+         "cudaError_t launch_pointwise_stiff(const PointwiseArgs<T>& a, cudaStream_t s);",
+         "3b4adf934a5f9f891d469b0c982ddfc580bb2d9a59fc11b22a84becd7c62462b"),
+    ]),
 }
 
 
@@ -200,12 +205,15 @@ def measured_traffic(cls, prec, size):
     if ent is None:
         return None
     root = os.path.dirname(os.path.abspath(__file__))
-    for rel, digest in ent[1].items():
+    for rel, start, end, digest in ent[1]:
         try:
-            with open(os.path.join(root, rel), "rb") as f:
-                if hashlib.sha256(f.read()).hexdigest() != digest:
-                    return None
-        except OSError:
+            with open(os.path.join(root, rel)) as f:
+                text = f.read()
+            i = text.index(start)
+            region = text[i:text.index(end, i)]
+        except (OSError, ValueError):
+            return None
+        if hashlib.sha256(region.encode()).hexdigest() != digest:
             return None
     return ent[0]
 
@@ -357,6 +365,33 @@ def run_ours(args):
     Ha.close()
     del qa, Aw, v64, f_out, v32, f32, dd
 
+    # the embedded-domain workload at full size: 12 spheres in a 256^3 box,
+    # quadratic basis, a = 3h (set-up and K.u; its solves do not converge, see the
+    # design notes on DNI with the quadratic basis)
+    sph = W.spheres_problem(n_box=args.size, n_spheres=12, a_tilde=3.0, degree=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Hs = rk.Handle.from_problem(sph, device=dev)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    spheres = {"n_omega": sph.n_omega, "setup_s": setup_s}
+    for dt_name, tdt in (("f32", torch.float32), ("f64", torch.float64)):
+        x = torch.rand(sph.nbox, dtype=tdt, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(2):
+            Hs.apply_K(x, y)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10 if tdt == torch.float32 else 3
+        a0.record(stream)
+        for _ in range(reps):
+            Hs.apply_K(x, y)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        spheres[f"kU_{dt_name}_ms"] = a0.elapsed_time(a1) / reps
+        del x, y
+    Hs.close()
+    del sph
+
     # isolated K.u rates (resident d, f)
     H = rk.Handle(p.n, p.h, chi, cg, V, 1, 2.5)
     kd = {}
@@ -464,6 +499,7 @@ def run_ours(args):
             "kU_isolated": kd,
             "cufft_comparison": cufft,
             "appendix_ops": appendix,
+            "spheres256_quadratic": spheres,
             "profiled_step_ms": profiled_ms,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
