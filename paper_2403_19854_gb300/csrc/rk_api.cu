@@ -172,6 +172,7 @@ struct rk_handle {
   double* trans64 = nullptr;
   float* trans32 = nullptr;
   double* part2 = nullptr;
+  double* mlumped = nullptr;  // M^l, computed once (Alg. C.2)
   // staging of host arrays
   double* stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   unsigned long long* counters = nullptr;  // singular count, first singular
@@ -1330,9 +1331,12 @@ rk_status transient_explicit(rk_handle* h, const double* f, const double* g, dou
                              cudaStream_t s) {
   RK_TRY(ensure_transient(h));
   const long long n = h->nbox;
-  double* ml = h->trans64 + (size_t)1 * n;
+  if (!h->mlumped) {
+    RK_TRY(h->alloc(&h->mlumped, (size_t)n));
+    RK_TRY(lumped_mass(h, h->mlumped, s));
+  }
+  const double* ml = h->mlumped;
   double* Kd = h->trans64 + (size_t)2 * n;
-  RK_TRY(lumped_mass(h, ml, s));
   if (g) RK_CK(launch_dirichlet_d0(h->trans64 + (size_t)3 * n, g, h->chi_gamma, n, s));
   // d = g on Gamma_g, 0 off chi (d keeps its free values)
   if (g) {
@@ -1990,6 +1994,7 @@ rk_status rk_clone(const rk_handle* parent, rk_handle** out) {
   h->trans64 = nullptr;
   h->trans32 = nullptr;
   h->part2 = nullptr;
+  h->mlumped = nullptr;
   for (int k = 0; k < 2; ++k) {
     h->tmaps32[k].clear();
     h->tmaps64[k].clear();
