@@ -132,14 +132,29 @@ struct rk_handle {
   float* coef32[3] = {nullptr, nullptr, nullptr};
   cpx<double>* tw64[3] = {nullptr, nullptr, nullptr};
   cpx<float>* tw32[3] = {nullptr, nullptr, nullptr};
-  // compressed coefficients of the fused z pass (see ZArgs): node class / index,
-  // table of the irregular nodes, interior values
+  // compressed coefficients of the pointwise stage: node class / index, table of
+  // the irregular nodes, interior values
   int* cidx = nullptr;
   double* ctab64 = nullptr;
   float* ctab32 = nullptr;
   long long n_irr = 0;
   double breg64[31] = {};
   float breg32[31] = {};
+  // Regular nodes see a support symmetric about them, so their odd moments vanish
+  // and b^k_q = 0 for q != 1+k: there g_{1+k} = c_k D_{1+k}, c_k = chi V (b^k_{1+k})^2,
+  // and every other g_p = 0.  The z table then carries, at row zrow_scaled[k], c_k
+  // times the row of D_{1+k}, so the z SPLIT of Alg. 2 writes the regular nodes'
+  // g directly (diag_reg; zrows rows in the z table).
+  bool diag_reg = false;
+  // bit g: nodes 4g .. 4g + 3 all regular / all outside chi (one spare word at the
+  // end); pw_list: the other groups, in order
+  uint32_t* regbits = nullptr;
+  uint32_t* outbits = nullptr;
+  int* pw_list = nullptr;
+  long long pw_count = 0;
+  int zrow_scaled[3] = {-1, -1, -1};
+  int zrows = 0;
+  double inv_c[3] = {0.0, 0.0, 0.0};
   // workspaces of the operator chains: X outputs, Y outputs, z-pass outputs
   double* ws64 = nullptr;
   float* ws32 = nullptr;
@@ -356,12 +371,17 @@ bool tile_maps_for(rk_handle* h, int axis, const PassArgs<T>& a, TileMaps* tm) {
   return true;
 }
 
+// pw: the z SPLIT of Alg. 2 also applies the pointwise stage (profiled as such)
 template <typename T>
-rk_status run_split(rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s) {
-  ProfScope ps(h, prof_cls<T>(axis == 0 ? RK_PROF_X_SPLIT : (axis == 1 ? RK_PROF_Y_SPLIT : RK_PROF_Z_SPLIT)), s);
+rk_status run_split(rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s,
+                    const PointwiseArgs<T>* pw = nullptr) {
+  ProfScope ps(h,
+               prof_cls<T>(pw ? RK_PROF_Z_STIFF
+                              : (axis == 0 ? RK_PROF_X_SPLIT : (axis == 1 ? RK_PROF_Y_SPLIT : RK_PROF_Z_SPLIT))),
+               s);
   TileMaps tm;
   const bool use = tile_maps_for<T>(h, axis, a, &tm);
-  cudaError_t e = launch_split<T>(axis, h->n[axis], a, s, use ? &tm : nullptr);
+  cudaError_t e = launch_split<T>(axis, h->n[axis], a, s, use ? &tm : nullptr, pw);
   return e == cudaSuccess ? RK_OK : cuda_fail(e, "split pass");
 }
 template <typename T>
@@ -531,7 +551,6 @@ rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uin
     }
   }
   az.g_begin[c.nY] = q;
-  RK_TRY(run_split<T>(h, 2, az, s));
   PointwiseArgs<T> pw;
   memset(&pw, 0, sizeof(pw));
   for (int p = 0; p < h->s; ++p) pw.D[p] = h->ws<T>(dbase + p);
@@ -541,7 +560,24 @@ rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uin
   pw.n_irr = h->n_irr;
   for (int j = 0; j < 3 * h->s + 1; ++j) pw.breg[j] = breg_of<T>(h, j);
   pw.nbox = h->nbox;
-  {
+  if (h->n[0] % 4 == 0 && h->diag_reg) {
+    // with diagonal interior coefficients the z SPLIT writes g_x, g_y, g_z of the
+    // regular nodes directly (scaled multiplier rows) and zeroes the rest of the
+    // regular and outside groups; the boundary groups follow in a short kernel
+    for (int qq = 0; qq < q; ++qq)
+      for (int k = 0; k < 3; ++k)
+        if (az.term_io[qq] == 1 + k) az.term_m[qq] = h->zrow_scaled[k];
+    az.coef_rows = h->zrows;
+    pw.diag = 1;
+    pw.regbits = h->regbits;
+    pw.outbits = h->outbits;
+    for (int k = 0; k < 3; ++k) pw.inv_c[k] = (T)h->inv_c[k];
+    RK_TRY(run_split<T>(h, 2, az, s, &pw));
+    ProfScope ps(h, prof_cls<T>(RK_PROF_Z_STIFF), s);
+    cudaError_t e = launch_pointwise_groups<T>(pw, h->pw_list, h->pw_count, s);
+    if (e != cudaSuccess) return cuda_fail(e, "pointwise stage");
+  } else {
+    RK_TRY(run_split<T>(h, 2, az, s));
     ProfScope ps(h, prof_cls<T>(RK_PROF_Z_STIFF), s);
     cudaError_t e = launch_pointwise_stiff<T>(pw, s);
     if (e != cudaSuccess) return cuda_fail(e, "pointwise stage");
@@ -1619,6 +1655,87 @@ rk_status compress_coefficients(rk_handle* h, cudaStream_t s) {
   return done(RK_OK);
 }
 
+// Regular-node fast path of the pointwise stage (see rk_handle::diag_reg).  The
+// support of a regular node is symmetric about it, so its odd moments (Eq. 48)
+// vanish and b^k_q = 0 for q != 1+k exactly; the computed values are the FFT
+// rounding of those zeros and are set to 0 (a check rejects anything above 1e-8
+// of the diagonal).  Then appends to the z table the rows c_k T_{alpha_z(1+k)}, at
+// indices of the same parity as alpha_z(1+k) (odd rows are imaginary spectra,
+// Eq. 55).
+rk_status scale_regular_rows(rk_handle* h, cudaStream_t s) {
+  const int S = h->s, mmax = 2 * h->degree;
+  h->zrows = mmax + 1;
+  h->diag_reg = false;
+  if (!(h->breg64[3 * S] > 0.0)) return RK_OK;  // no regular node
+  for (int k = 0; k < 3; ++k) {
+    const double dk = h->breg64[k * S + 1 + k];
+    if (!(std::fabs(dk) > 0.0)) return RK_OK;
+    for (int q = 0; q < S; ++q)
+      if (q != 1 + k && !(std::fabs(h->breg64[k * S + q]) <= 1e-8 * std::fabs(dk))) return RK_OK;
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int q = 0; q < S; ++q)
+      if (q != 1 + k) {
+        h->breg64[k * S + q] = 0.0;
+        h->breg32[k * S + q] = 0.0f;
+      }
+  std::vector<double> coef;
+  std::vector<cpx<double>> tw;
+  axis_tables(h->n[2], h->a_tilde, h->reach, mmax, coef, tw);
+  const int n = h->n[2];
+  int next[2] = {mmax + 1 + ((mmax + 1) % 2), mmax + 1 + ((mmax + 2) % 2)};  // next free even, odd row
+  int rows = mmax + 1;
+  double c[3];
+  for (int k = 0; k < 3; ++k) {
+    const int mz = h->chain.alpha[1 + k][2];
+    h->zrow_scaled[k] = next[mz & 1];
+    next[mz & 1] += 2;
+    rows = std::max(rows, h->zrow_scaled[k] + 1);
+    c[k] = h->breg64[3 * S] * h->breg64[k * S + 1 + k] * h->breg64[k * S + 1 + k];
+    h->inv_c[k] = 1.0 / c[k];
+  }
+  coef.resize((size_t)rows * n, 0.0);
+  for (int k = 0; k < 3; ++k) {
+    const int mz = h->chain.alpha[1 + k][2];
+    for (int i = 0; i < n; ++i) coef[(size_t)h->zrow_scaled[k] * n + i] = c[k] * coef[(size_t)mz * n + i];
+  }
+  std::vector<float> coef32(coef.begin(), coef.end());
+  rk_status st;
+  if ((st = h->alloc(&h->coef64[2], coef.size())) != RK_OK || (st = h->alloc(&h->coef32[2], coef.size())) != RK_OK)
+    return st;
+  if (h->nbox % 4 == 0) {
+    const long long ng = h->nbox / 4;
+    const size_t nwords = (size_t)((ng + 31) / 32) + 1;
+    const int nblk = (int)((ng + kScanBlock - 1) / kScanBlock);
+    uint8_t* gcls = nullptr;
+    int* counts = nullptr;
+    int total = 0;
+    if ((st = h->alloc(&h->regbits, nwords)) != RK_OK || (st = h->alloc(&h->outbits, nwords)) != RK_OK) return st;
+    cudaError_t er = cudaMalloc((void**)&gcls, (size_t)ng);
+    if (er == cudaSuccess) er = cudaMalloc((void**)&counts, sizeof(int) * ((size_t)nblk + 1));
+    if (er == cudaSuccess) er = cudaMemsetAsync(h->regbits, 0, nwords * sizeof(uint32_t), s);
+    if (er == cudaSuccess) er = cudaMemsetAsync(h->outbits, 0, nwords * sizeof(uint32_t), s);
+    if (er == cudaSuccess) er = launch_group_class(gcls, h->regbits, h->outbits, h->cidx, ng, s);
+    if (er == cudaSuccess) er = launch_count_irregular(gcls, ng, counts, s);
+    if (er == cudaSuccess) er = launch_scan_counts(counts, nblk, counts + nblk, s);
+    if (er == cudaSuccess) er = cudaMemcpyAsync(&total, counts + nblk, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (er == cudaSuccess) er = cudaStreamSynchronize(s);
+    if (er == cudaSuccess && (st = h->alloc(&h->pw_list, (size_t)total)) != RK_OK) er = cudaErrorMemoryAllocation;
+    if (er == cudaSuccess) er = launch_list_compact(gcls, counts, ng, h->pw_list, s);
+    if (er == cudaSuccess) er = cudaStreamSynchronize(s);
+    cudaFree(gcls);
+    cudaFree(counts);
+    if (er != cudaSuccess) return cuda_fail(er, "group classes");
+    h->pw_count = total;
+  }
+  cudaError_t e = cudaMemcpy(h->coef64[2], coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->coef32[2], coef32.data(), coef32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "copy z table");
+  h->zrows = rows;
+  h->diag_reg = h->regbits != nullptr;
+  return RK_OK;
+}
+
 // Vector-Jacobian product of the solve map (r, g) -> u^h for a cotangent e on the
 // grid (already masked by chi): w = U^T e (transpose of Alg. 3), one adjoint solve
 // A lambda = chi_Omega o w (A = chi_Omega K chi_Omega is symmetric), then
@@ -1952,6 +2069,7 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
   cudaFree(mws);
   if (st != RK_OK) return bail(st);
   if ((st = compress_coefficients(h, s)) != RK_OK) return bail(st);
+  if ((st = scale_regular_rows(h, s)) != RK_OK) return bail(st);
   *out = h;
   if (h->n_singular)
     return fail(RK_ERR_SINGULAR_MOMENT,

@@ -7,10 +7,11 @@ namespace rk {
 RK_FOR_EACH_LENGTH(RK_DECLARE_LENGTH)
 
 template <typename T>
-cudaError_t launch_split(int axis, int n, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps) {
+cudaError_t launch_split(int axis, int n, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps,
+                         const PointwiseArgs<T>* pw) {
   switch (n) {
 #define RK_CASE(N) \
-  case N: return split_n<T, N>(axis, a, s, maps);
+  case N: return split_n<T, N>(axis, a, s, maps, pw);
     RK_FOR_EACH_LENGTH(RK_CASE)
 #undef RK_CASE
     default: return cudaErrorInvalidValue;
@@ -61,8 +62,10 @@ cudaError_t launch_pfft(int mode, int n, const PfftArgs<T>& a, cudaStream_t s) {
   }
 }
 
-template cudaError_t launch_split<float>(int, int, const PassArgs<float>&, cudaStream_t, const TileMaps*);
-template cudaError_t launch_split<double>(int, int, const PassArgs<double>&, cudaStream_t, const TileMaps*);
+template cudaError_t launch_split<float>(int, int, const PassArgs<float>&, cudaStream_t, const TileMaps*,
+                                        const PointwiseArgs<float>*);
+template cudaError_t launch_split<double>(int, int, const PassArgs<double>&, cudaStream_t, const TileMaps*,
+                                         const PointwiseArgs<double>*);
 template cudaError_t launch_merge<float>(int, int, const PassArgs<float>&, cudaStream_t, const TileMaps*);
 template cudaError_t launch_merge<double>(int, int, const PassArgs<double>&, cudaStream_t, const TileMaps*);
 template cudaError_t launch_z<float>(int, int, const ZArgs<float>&, cudaStream_t);

@@ -26,7 +26,9 @@ bool supported_length(int n);
 
 // axis: 0 = x (contiguous lines), 1 = y, 2 = z (strided lines)
 template <typename T>
-cudaError_t launch_split(int axis, int n, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps = nullptr);
+// pw (z SPLIT of Alg. 2 only): apply the pointwise stage to each tile written
+cudaError_t launch_split(int axis, int n, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps = nullptr,
+                         const PointwiseArgs<T>* pw = nullptr);
 template <typename T>
 cudaError_t launch_merge(int axis, int n, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps = nullptr);
 template <typename T>
@@ -58,6 +60,13 @@ cudaError_t launch_erode(uint8_t* out, const uint8_t* in, int axis, int r, const
 // cls = 0 (chi = 0), 1 (regular: eroded and V == vreg), 2 (irregular)
 cudaError_t launch_classify(uint8_t* cls, const uint8_t* chi, const uint8_t* eroded, const double* V, double vreg,
                             long long n, cudaStream_t s);
+// 4-node groups g (nodes 4g .. 4g + 3): gcls = 0 all regular, 1 all outside chi,
+// 2 other; bit g of regbits / outbits (one word per 32 groups) marks 0 / 1
+cudaError_t launch_group_class(uint8_t* gcls, uint32_t* regbits, uint32_t* outbits, const int* cidx, long long ngroups,
+                               cudaStream_t s);
+// ordered indices of the entries with cls == 2 (offsets from launch_count_irregular
+// and launch_scan_counts over the same array)
+cudaError_t launch_list_compact(const uint8_t* cls, const int* offsets, long long n, int* list, cudaStream_t s);
 constexpr int kScanBlock = 1024;  // nodes per compaction block
 // per-block counts of class 2 -> counts[nblk]
 cudaError_t launch_count_irregular(const uint8_t* cls, long long n, int* counts, cudaStream_t s);
@@ -76,23 +85,10 @@ cudaError_t launch_gather(double* out, const double* src, long long stride, long
 // with the coefficients of a node from breg (cidx = 0), from row cidx - 1 of ctab
 // (cidx > 0), or g = 0 off chi (cidx = -1).
 template <typename T>
-struct PointwiseArgs {
-  T* D[10];
-  int s;
-  const int* cidx;   // per node: -1 outside chi, 0 regular, 1 + row of ctab
-  const T* ctab;     // [n_irr][ctab_pitch<T>(s)]: b^x_p, b^y_p, b^z_p (s each), chi V, zero padding
-  long long n_irr;
-  T breg[31];        // the 3s+1 values of a regular node
-  long long nbox;
-};
-// Row pitch of the table of irregular nodes: 3s+1 values padded to whole 16-byte
-// vectors, so that a row is read with 16-byte loads.
-template <typename T>
-constexpr int ctab_pitch(int s) {
-  return (3 * s + 1 + (int)(16 / sizeof(T)) - 1) / (int)(16 / sizeof(T)) * (int)(16 / sizeof(T));
-}
-template <typename T>
 cudaError_t launch_pointwise_stiff(const PointwiseArgs<T>& a, cudaStream_t s);
+// the pointwise stage on the listed 4-node groups only (after a z SPLIT with diag)
+template <typename T>
+cudaError_t launch_pointwise_groups(const PointwiseArgs<T>& a, const int* list, long long count, cudaStream_t s);
 
 // ------------------------------------------------------------ CG kernels
 

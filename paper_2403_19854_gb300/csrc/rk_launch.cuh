@@ -27,7 +27,9 @@ struct Cfg<double> {
 
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  // static plus dynamic shared memory above 48 KB needs the opt-in; the kernels
+  // here use less than 16 KB of static shared memory
+  if (bytes <= 32 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -35,14 +37,14 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
 // occupancy of the kernel is queried on first use), each looping over tiles of
 // 2L x values times one index of the other axis.  a16: every row of every input
 // starts on a 16-byte boundary (16-byte async copies), else per-element copies.
-template <typename T, int N, bool MERGE>
-cudaError_t launch_strided(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps) {
+template <typename T, int N, bool MERGE, int PW = 0>
+cudaError_t launch_strided(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps,
+                           const PointwiseArgs<T>* pw = nullptr) {
   constexpr int L = Cfg<T>::L;
   using S = Strided<T, N, L>;
-  auto kernel = MERGE ? k_strided_merge<T, N, L> : k_strided_split<T, N, L>;
   static int resident = 0;  // blocks per SM of this kernel (first device used)
   static int sms = 0;
-  if (!resident) {
+  auto occupancy = [&](auto kernel) -> cudaError_t {
     cudaError_t e = set_smem(kernel, S::SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0, nb = 0, nsm = 0;
@@ -51,6 +53,15 @@ cudaError_t launch_strided(int axis, const PassArgs<T>& a, cudaStream_t s, const
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, S::THREADS, S::SMEM)) != cudaSuccess) return e;
     sms = nsm;
     resident = nb > 0 ? nb : 1;
+    return cudaSuccess;
+  };
+  if (!resident) {
+    cudaError_t e;
+    if constexpr (MERGE)
+      e = occupancy(k_strided_merge<T, N, L>);
+    else
+      e = occupancy(k_strided_split<T, N, L, PW>);
+    if (e != cudaSuccess) return e;
   }
   const int nbx = (a.nx + S::ROW - 1) / S::ROW;
   const long long ntiles = (long long)nbx * (axis == 1 ? a.nz : a.ny);
@@ -60,8 +71,14 @@ cudaError_t launch_strided(int axis, const PassArgs<T>& a, cudaStream_t s, const
   const long long cap = (long long)resident * sms;
   const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
   static const TileMaps none = {};
+  static const PointwiseArgs<T> no_pw = {};
   count_launch();
-  kernel<<<grid, S::THREADS, S::SMEM, s>>>(a, nbx, ntiles, a16 ? 1 : 0, maps ? *maps : none, maps ? axis : 0);
+  if constexpr (MERGE)
+    k_strided_merge<T, N, L><<<grid, S::THREADS, S::SMEM, s>>>(a, nbx, ntiles, a16 ? 1 : 0, maps ? *maps : none,
+                                                               maps ? axis : 0);
+  else
+    k_strided_split<T, N, L, PW><<<grid, S::THREADS, S::SMEM, s>>>(a, nbx, ntiles, a16 ? 1 : 0, maps ? *maps : none,
+                                                                   maps ? axis : 0, pw ? *pw : no_pw);
   return cudaGetLastError();
 }
 
@@ -83,7 +100,7 @@ bool x_bulk_setup(PassArgs<T>& b) {
 }
 
 template <typename T, int N>
-cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps) {
+cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMaps* maps, const PointwiseArgs<T>* pw) {
   if (axis == 0) {
     constexpr int LX = Cfg<T>::XTHREADS / LineShape<N>::P;
     using X = XPass<T, N, LX>;
@@ -92,10 +109,10 @@ cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMa
     PassArgs<T> b = a;
     if (x_bulk_setup<T, N, LX>(b)) {
       auto k = k_x_split<T, N, LX, true>;
-      cudaError_t e = set_smem(k, X::SMEM + 2 * X::TILE);
+      cudaError_t e = set_smem(k, X::SMEM_FEED);
       if (e != cudaSuccess) return e;
       count_launch();
-      k<<<nb, X::THREADS, X::SMEM + 2 * X::TILE, s>>>(b);
+      k<<<nb, X::THREADS, X::SMEM_FEED, s>>>(b);
     } else {
       auto k = k_x_split<T, N, LX, false>;
       cudaError_t e = set_smem(k, X::SMEM);
@@ -104,6 +121,8 @@ cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMa
       k<<<nb, X::THREADS, X::SMEM, s>>>(b);
     }
   } else {
+    if (pw && pw->s == 4) return launch_strided<T, N, false, 4>(axis, a, s, maps, pw);
+    if (pw && pw->s == 10) return launch_strided<T, N, false, 10>(axis, a, s, maps, pw);
     return launch_strided<T, N, false>(axis, a, s, maps);
   }
   return cudaGetLastError();
@@ -205,8 +224,10 @@ cudaError_t pfft_n(int mode, const PfftArgs<T>& a, cudaStream_t s) {
 #define RK_FOR_EACH_LENGTH(X) X(8) X(16) X(32) X(36) X(48) X(64) X(72) X(96) X(100) X(128) X(144) X(162) X(256)
 
 #define RK_DECLARE_LENGTH(N)                                                                  \
-  extern template cudaError_t split_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*);   \
-  extern template cudaError_t split_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*); \
+  extern template cudaError_t split_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*,             \
+                                               const PointwiseArgs<float>*);   \
+  extern template cudaError_t split_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*,           \
+                                                const PointwiseArgs<double>*); \
   extern template cudaError_t merge_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*);   \
   extern template cudaError_t merge_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*); \
   extern template cudaError_t z_n<float, N>(int, const ZArgs<float>&, cudaStream_t);          \
@@ -217,8 +238,10 @@ cudaError_t pfft_n(int mode, const PfftArgs<T>& a, cudaStream_t s) {
   extern template cudaError_t pfft_n<double, N>(int, const PfftArgs<double>&, cudaStream_t);
 
 #define RK_INSTANTIATE_LENGTH(N)                                                       \
-  template cudaError_t split_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*);   \
-  template cudaError_t split_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*); \
+  template cudaError_t split_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*,             \
+                                               const PointwiseArgs<float>*);   \
+  template cudaError_t split_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*,           \
+                                                const PointwiseArgs<double>*); \
   template cudaError_t merge_n<float, N>(int, const PassArgs<float>&, cudaStream_t, const TileMaps*);   \
   template cudaError_t merge_n<double, N>(int, const PassArgs<double>&, cudaStream_t, const TileMaps*); \
   template cudaError_t z_n<float, N>(int, const ZArgs<float>&, cudaStream_t);          \

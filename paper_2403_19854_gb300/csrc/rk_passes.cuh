@@ -11,9 +11,9 @@
 //          (one output per table)                -- the forward chain of Alg. 1-3;
 //   MERGE: several inputs, each with its table, are summed in the spectrum and
 //          transformed back once                 -- the reflected chain of Alg. 2, 4.
-// The z pass of Alg. 2 additionally performs the pointwise stage between the two
-// chains (A^k = sum_q b^k_q D_q, Eq. 90; C^k_p A^k, Eq. 91) without leaving the
-// chip.
+// The z SPLIT of Alg. 2 also applies the pointwise stage between the two chains
+// (A^k = sum_q b^k_q D_q, Eq. 90; C^k_p A^k, Eq. 91) to every tile it has just
+// written, while the tile's values are still in L2.
 //
 // Data: real fields on the periodic box, x fastest (idx = i + nx*(j + ny*k)).
 // Two real lines are packed into one complex line (re = line 0, im = line 1);
@@ -23,6 +23,7 @@
 #pragma once
 
 #include "rk_linefft.cuh"
+#include "rk_pointwise.cuh"
 #include "rk_tma.cuh"
 
 namespace rk {
@@ -127,7 +128,7 @@ struct Strided {
   // shared memory once per block (the large shared-memory carve-out of these
   // kernels leaves little L1 for them; 2-3 % faster)
   static constexpr bool STAGE = sizeof(T) == 4;
-  static constexpr int COEF_ROWS_MAX = 5;
+  static constexpr int COEF_ROWS_MAX = 7;
   static constexpr size_t SMEM_CT = STAGE ? sizeof(T) * (size_t)COEF_ROWS_MAX * N + sizeof(cpx<T>) * (size_t)N : 0;
   static constexpr size_t SMEM = SMEM_BUF + SMEM_TILE + SMEM_CT;
   // copy coef / tw to shared memory; returns the pointers the block should use
@@ -232,14 +233,23 @@ struct TileFeed {
   }
 };
 
-template <typename T, int N, int L>
+// PW > 0 (z SPLIT of Alg. 2, PW = s, diagonal interior coefficients): the
+// multiplier rows of D_x, D_y, D_z carry c_k, so at regular nodes the pass writes
+// g_x, g_y, g_z of Eq. 91 directly; once a tile is written the block sets the
+// other g_p of its regular 4-node groups, and every g_p of its groups outside chi,
+// to 0.  The remaining groups (boundary layers) are left to k_pointwise_groups.
+// Requires n_x to be a multiple of 4.
+template <typename T, int N, int L, int PW>
 __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::MIN_BLOCKS_SPLIT)
     k_strided_split(const PassArgs<T> a, const int nbx, const long long ntiles, const int a16,
-                    const __grid_constant__ TileMaps maps, const int tma_axis) {
+                    const __grid_constant__ TileMaps maps, const int tma_axis,
+                    const __grid_constant__ PointwiseArgs<T> pw) {
   using S = Strided<T, N, L>;
   using F = typename S::F;
   RK_DYN_SMEM(unsigned char, smem);
   __shared__ uint64_t bar;
+  // per tile row: its all-regular / all-outside 4-node groups, a bit per group
+  __shared__ uint8_t rflag[PW > 0 ? N : 1], oflag[PW > 0 ? N : 1];
   TileFeed<T, N, L> feed{reinterpret_cast<T*>(smem), &bar, 0u, tma_axis};
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem + S::SMEM_TILE);
   const int l = threadIdx.x % L, t = threadIdx.x / L;
@@ -280,6 +290,35 @@ __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::M
         if (ok)
 #pragma unroll
           for (int r = 0; r < S::R; ++r) S::store(out, base + F::nat_pos(t, r) * a.line_stride, w[r]);
+      }
+    }
+    if (PW > 0) {
+      constexpr int VEC = 16 / sizeof(T);
+      constexpr int VPR = S::ROW / VEC;  // vectors per tile row
+      constexpr int SP = PW > 0 ? PW : 1;
+      const int nv = min(S::ROW, a.nx - x0) / VEC;
+      const long long tb = x0 + (tile / nbx) * a.other_stride;
+      // a row's ROW / 4 <= 8 groups start at bit g0 = (tb + row * line_stride) / 4
+      // and span at most two bytes of the bit arrays (one spare word at their end)
+      const uint8_t* rb = reinterpret_cast<const uint8_t*>(pw.regbits);
+      const uint8_t* ob = reinterpret_cast<const uint8_t*>(pw.outbits);
+      for (int row = threadIdx.x; row < N; row += S::THREADS) {
+        const long long g0 = (tb + row * a.line_stride) / 4;
+        const unsigned r2 = (unsigned)__ldg(rb + g0 / 8) | ((unsigned)__ldg(rb + g0 / 8 + 1) << 8);
+        const unsigned o2 = (unsigned)__ldg(ob + g0 / 8) | ((unsigned)__ldg(ob + g0 / 8 + 1) << 8);
+        rflag[row] = (uint8_t)(r2 >> (g0 % 8));
+        oflag[row] = (uint8_t)(o2 >> (g0 % 8));
+      }
+      RK_SYNC();  // the flags are in place (and every D_p of the tile is written)
+      for (int j = threadIdx.x; j < N * VPR; j += S::THREADS) {
+        const int row = j / VPR, c = j % VPR;
+        if (c >= nv) continue;
+        const long long i0 = tb + row * a.line_stride + c * VEC;
+        const int bit = c * VEC / 4;
+        if ((rflag[row] >> bit) & 1u)
+          pointwise_vec_regular<T, SP>(pw, i0);
+        else if ((oflag[row] >> bit) & 1u)
+          pointwise_vec_zero<T, SP>(pw, i0);
       }
     }
   }
@@ -360,6 +399,7 @@ struct XPass {
   static constexpr int ROWS = 2 * LX;
   static constexpr int PITCH = N + 32 / (int)sizeof(T);
   static constexpr size_t TILE = sizeof(T) * (size_t)ROWS * PITCH;
+  static constexpr size_t SMEM_FEED = SMEM > 2 * TILE ? SMEM : 2 * TILE;
   // resident blocks per SM the register allocation must allow
   static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 4 : 3;
 };
@@ -495,7 +535,9 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
   using F = typename X::F;
   RK_DYN_SMEM(unsigned char, smem);
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem);
-  T* tileA = reinterpret_cast<T*>(smem + X::SMEM);
+  // the row tiles share the transpose buffer's memory: every tile read happens
+  // before the forward transform, whose first barrier precedes any buffer write
+  T* tileA = reinterpret_cast<T*>(smem);
   T* tileB = tileA + X::ROWS * X::PITCH;
   __shared__ uint64_t bar;
   const int t = threadIdx.x % X::P, l = threadIdx.x / X::P;

@@ -61,6 +61,69 @@ cudaError_t launch_classify(uint8_t* cls, const uint8_t* chi, const uint8_t* ero
   return cudaGetLastError();
 }
 
+// Classes of the 4-node groups g (nodes 4g .. 4g + 3): 0 all regular (cidx == 0),
+// 1 all outside chi (cidx == -1), 2 any other; bit g of regbits / outbits marks
+// classes 0 / 1.  One thread per 32 groups.
+__global__ void k_group_class(uint8_t* gcls, uint32_t* regbits, uint32_t* outbits, const int* cidx, long long ngroups) {
+  const long long nwords = (ngroups + 31) / 32;
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += (long long)gridDim.x * blockDim.x) {
+    uint32_t rv = 0u, ov = 0u;
+    for (int j = 0; j < 32; ++j) {
+      const long long g = w * 32 + j;
+      if (g >= ngroups) break;
+      const int4 c = *reinterpret_cast<const int4*>(cidx + 4 * g);
+      const bool reg = c.x == 0 && c.y == 0 && c.z == 0 && c.w == 0;
+      const bool out = c.x == -1 && c.y == -1 && c.z == -1 && c.w == -1;
+      rv |= (reg ? 1u : 0u) << j;
+      ov |= (out ? 1u : 0u) << j;
+      gcls[g] = reg ? 0 : (out ? 1 : 2);
+    }
+    regbits[w] = rv;
+    outbits[w] = ov;
+  }
+}
+cudaError_t launch_group_class(uint8_t* gcls, uint32_t* regbits, uint32_t* outbits, const int* cidx, long long ngroups,
+                               cudaStream_t s) {
+  const long long nwords = (ngroups + 31) / 32;
+  const long long nb = (nwords + 255) / 256;
+  count_launch();
+  k_group_class<<<(unsigned)(nb < 152 * 32 ? (nb > 0 ? nb : 1) : 152 * 32), 256, 0, s>>>(gcls, regbits, outbits, cidx,
+                                                                                         ngroups);
+  return cudaGetLastError();
+}
+
+// ordered list of the entries with cls == 2 (offsets: exclusive scan of the
+// per-block counts of k_count_irregular); one block per kScanBlock entries
+__global__ void __launch_bounds__(256) k_list_compact(const uint8_t* cls, const int* offsets, long long n, int* list) {
+  __shared__ int sh[256];
+  const long long b0 = (long long)blockIdx.x * kScanBlock;
+  constexpr int PER = kScanBlock / 256;
+  int c = 0;
+  for (int j = 0; j < PER; ++j) {
+    const long long i = b0 + threadIdx.x * PER + j;
+    c += (i < n && cls[i] == 2) ? 1 : 0;
+  }
+  sh[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const int v = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int pos = offsets[blockIdx.x] + sh[threadIdx.x] - c;
+  for (int j = 0; j < PER; ++j) {
+    const long long i = b0 + threadIdx.x * PER + j;
+    if (i < n && cls[i] == 2) list[pos++] = (int)i;
+  }
+}
+cudaError_t launch_list_compact(const uint8_t* cls, const int* offsets, long long n, int* list, cudaStream_t s) {
+  const long long nblk = (n + kScanBlock - 1) / kScanBlock;
+  count_launch();
+  k_list_compact<<<(unsigned)nblk, 256, 0, s>>>(cls, offsets, n, list);
+  return cudaGetLastError();
+}
+
 // block b counts the irregular nodes of [b*kScanBlock, (b+1)*kScanBlock)
 __global__ void __launch_bounds__(256) k_count_irregular(const uint8_t* cls, long long n, int* counts) {
   __shared__ int sh[256];
@@ -187,72 +250,44 @@ cudaError_t launch_gather(double* out, const double* src, long long stride, long
 // Each thread owns VEC consecutive nodes (one 16-byte vector per field).
 template <typename T, int S>
 __global__ void __launch_bounds__(256) k_pointwise_stiff(const PointwiseArgs<T> a) {
-  constexpr int VEC = 16 / sizeof(T);        // nodes per thread and values per 16-byte vector
-  constexpr int NC = 3 * S + 1;              // b^x_p, b^y_p, b^z_p, chi V
-  constexpr int CP = ctab_pitch<T>(S);       // padded row of coefficients
-  using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-  __shared__ __align__(16) T br[CP];
-  for (int j = threadIdx.x; j < CP; j += blockDim.x) br[j] = j < NC ? a.breg[j] : (T)0;
+  constexpr int VEC = 16 / sizeof(T);  // nodes per thread and values per 16-byte vector
+  __shared__ __align__(16) T br[ctab_pitch<T>(S)];
+  pointwise_stage_breg<T, S>(a, br, threadIdx.x, blockDim.x);
   __syncthreads();
   const long long nv = a.nbox / VEC;
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
-    const long long i0 = v * VEC;
-    T d[S][VEC];
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x)
+    pointwise_vec<T, S, false>(a, br, v * VEC);
+}
+
+// The listed 4-node groups (neither all regular nor all outside chi) of a z SPLIT
+// that applied the regular / outside cases itself (a.diag: D_x, D_y, D_z scaled).
+template <typename T, int S>
+__global__ void __launch_bounds__(256) k_pointwise_groups(const PointwiseArgs<T> a, const int* list, long long count) {
+  constexpr int VEC = 16 / sizeof(T);
+  __shared__ __align__(16) T br[ctab_pitch<T>(S)];
+  pointwise_stage_breg<T, S>(a, br, threadIdx.x, blockDim.x);
+  __syncthreads();
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < count; j += (long long)gridDim.x * blockDim.x) {
+    const long long i0 = 4LL * list[j];
 #pragma unroll
-    for (int q = 0; q < S; ++q) {
-      const V16 raw = *reinterpret_cast<const V16*>(a.D[q] + i0);
-      memcpy(d[q], &raw, 16);
-    }
-    int ci[VEC];
-    if (VEC == 4) {
-      const int4 c4 = *reinterpret_cast<const int4*>(a.cidx + i0);
-      ci[0] = c4.x;
-      ci[1] = c4.y;
-      ci[VEC > 2 ? 2 : 0] = c4.z;
-      ci[VEC > 3 ? 3 : 0] = c4.w;
-    } else {
-      const int2 c2 = *reinterpret_cast<const int2*>(a.cidx + i0);
-      ci[0] = c2.x;
-      ci[1] = c2.y;
-    }
-    T g[S][VEC];
-#pragma unroll
-    for (int e = 0; e < VEC; ++e) {
-      const int c = ci[e];
-      // the node's coefficients: shared interior values or its row of the table
-      // (16-byte loads); the arithmetic below is the same for both
-      T co[CP];
-      if (c > 0) {
-        const V16* src = reinterpret_cast<const V16*>(a.ctab + (long long)(c - 1) * CP);
-#pragma unroll
-        for (int k = 0; k < CP / VEC; ++k) {
-          const V16 raw = __ldg(src + k);
-          memcpy(co + k * VEC, &raw, 16);
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < CP / VEC; ++k) {
-          const V16 raw = reinterpret_cast<const V16*>(br)[k];
-          memcpy(co + k * VEC, &raw, 16);
-        }
-      }
-      T A[3] = {(T)0, (T)0, (T)0};
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int q = 0; q < S; ++q) A[k] += co[k * S + q] * d[q][e];
-      const T cv = c >= 0 ? co[3 * S] : (T)0;  // chi V; 0 outside chi
-#pragma unroll
-      for (int p = 0; p < S; ++p) g[p][e] = cv * (co[p] * A[0] + co[S + p] * A[1] + co[2 * S + p] * A[2]);
-    }
-#pragma unroll
-    for (int p = 0; p < S; ++p) {
-      V16 raw;
-      memcpy(&raw, g[p], 16);
-      *reinterpret_cast<V16*>(a.D[p] + i0) = raw;
-    }
+    for (int v = 0; v < 4 / VEC; ++v) pointwise_vec<T, S, false>(a, br, i0 + v * VEC);
   }
 }
+
+template <typename T>
+cudaError_t launch_pointwise_groups(const PointwiseArgs<T>& a, const int* list, long long count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const long long nb = (count + 255) / 256;
+  const unsigned grid = (unsigned)(nb < 152 * 16 ? nb : 152 * 16);
+  count_launch();
+  if (a.s == 4)
+    k_pointwise_groups<T, 4><<<grid, 256, 0, s>>>(a, list, count);
+  else
+    k_pointwise_groups<T, 10><<<grid, 256, 0, s>>>(a, list, count);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pointwise_groups<float>(const PointwiseArgs<float>&, const int*, long long, cudaStream_t);
+template cudaError_t launch_pointwise_groups<double>(const PointwiseArgs<double>&, const int*, long long, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_pointwise_stiff(const PointwiseArgs<T>& a, cudaStream_t s) {
@@ -448,7 +483,7 @@ cudaError_t launch_nl_line(const double* u, const double* w, const double* V, co
 
 // 16-byte vectors of T (4 floats / 2 doubles)
 template <typename T>
-struct Vec16 {
+struct VecN {
   static constexpr int N = 16 / sizeof(T);
   T v[N];
 };
@@ -458,7 +493,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_xr_fused(T* __restrict__ x, 
                                                             const T* __restrict__ p, const T* __restrict__ Ap,
                                                             CGState* st, long long n, double* __restrict__ part,
                                                             unsigned* counter) {
-  using V = Vec16<T>;
+  using V = VecN<T>;
   const T al = (T)st->alpha;
   DotAccPair<T> acc;
   const long long nv = n / V::N;
