@@ -61,6 +61,42 @@ RK_DEV void pointwise_vec_regular(const PointwiseArgs<T>& a, long long i0) {
     if (p < 1 || p > 3) *reinterpret_cast<V16*>(a.D[p] + i0) = zero;
 }
 
+// The 3s+1 (padded) coefficients of a node of class c: its row of the table of
+// irregular nodes (c > 0) or the shared interior values (16-byte loads).
+template <typename T, int S>
+RK_DEV void pointwise_coefs(const PointwiseArgs<T>& a, const T* br, int c, T* co) {
+  constexpr int VEC = 16 / sizeof(T);
+  constexpr int CP = ctab_pitch<T>(S);
+  using V16 = Vec16<T>;
+  if (c > 0) {
+    const V16* src = reinterpret_cast<const V16*>(a.ctab + (long long)(c - 1) * CP);
+#pragma unroll
+    for (int k = 0; k < CP / VEC; ++k) {
+      const V16 raw = __ldg(src + k);
+      memcpy(co + k * VEC, &raw, 16);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < CP / VEC; ++k) {
+      const V16 raw = reinterpret_cast<const V16*>(br)[k];
+      memcpy(co + k * VEC, &raw, 16);
+    }
+  }
+}
+
+// Eq. 90-91 at one node: A^k = sum_q b^k_q d_q, g_p = chi V sum_k b^k_p A^k (0 off chi)
+template <typename T, int S>
+RK_DEV void pointwise_node(const T* co, int c, const T* d, T* g) {
+  T A[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int q = 0; q < S; ++q) A[k] += co[k * S + q] * d[q];
+  const T cv = c >= 0 ? co[3 * S] : (T)0;  // chi V; 0 outside chi
+#pragma unroll
+  for (int p = 0; p < S; ++p) g[p] = cv * (co[p] * A[0] + co[S + p] * A[1] + co[2 * S + p] * A[2]);
+}
+
 // Nodes outside chi: g_p = 0 for every p.
 template <typename T, int S>
 RK_DEV void pointwise_vec_zero(const PointwiseArgs<T>& a, long long i0) {
@@ -107,32 +143,14 @@ RK_DEV void pointwise_vec(const PointwiseArgs<T>& a, const T* br, long long i0) 
   T g[S][VEC];
 #pragma unroll
   for (int e = 0; e < VEC; ++e) {
-    const int c = ci[e];
-    // the node's coefficients: shared interior values or its row of the table
-    // (16-byte loads); the arithmetic below is the same for both
-    T co[CP];
-    if (c > 0) {
-      const V16* src = reinterpret_cast<const V16*>(a.ctab + (long long)(c - 1) * CP);
+    T co[ctab_pitch<T>(S)];
+    pointwise_coefs<T, S>(a, br, ci[e], co);
+    T de[S], ge[S];
 #pragma unroll
-      for (int k = 0; k < CP / VEC; ++k) {
-        const V16 raw = __ldg(src + k);
-        memcpy(co + k * VEC, &raw, 16);
-      }
-    } else {
+    for (int q = 0; q < S; ++q) de[q] = d[q][e];
+    pointwise_node<T, S>(co, ci[e], de, ge);
 #pragma unroll
-      for (int k = 0; k < CP / VEC; ++k) {
-        const V16 raw = reinterpret_cast<const V16*>(br)[k];
-        memcpy(co + k * VEC, &raw, 16);
-      }
-    }
-    T A[3] = {(T)0, (T)0, (T)0};
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int q = 0; q < S; ++q) A[k] += co[k * S + q] * d[q][e];
-    const T cv = c >= 0 ? co[3 * S] : (T)0;  // chi V; 0 outside chi
-#pragma unroll
-    for (int p = 0; p < S; ++p) g[p][e] = cv * (co[p] * A[0] + co[S + p] * A[1] + co[2 * S + p] * A[2]);
+    for (int p = 0; p < S; ++p) g[p][e] = ge[p];
   }
 #pragma unroll
   for (int p = 0; p < S; ++p) {

@@ -263,21 +263,31 @@ __global__ void __launch_bounds__(256) k_pointwise_stiff(const PointwiseArgs<T> 
 // that applied the regular / outside cases itself (a.diag: D_x, D_y, D_z scaled).
 template <typename T, int S>
 __global__ void __launch_bounds__(256) k_pointwise_groups(const PointwiseArgs<T> a, const int* list, long long count) {
-  constexpr int VEC = 16 / sizeof(T);
   __shared__ __align__(16) T br[ctab_pitch<T>(S)];
   pointwise_stage_breg<T, S>(a, br, threadIdx.x, blockDim.x);
   __syncthreads();
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < count; j += (long long)gridDim.x * blockDim.x) {
-    const long long i0 = 4LL * list[j];
+  // one node per thread: 4 threads per listed group
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < 4 * count;
+       j += (long long)gridDim.x * blockDim.x) {
+    const long long i = 4LL * __ldg(list + (j >> 2)) + (j & 3);
+    const int c = __ldg(a.cidx + i);
+    T d[S], g[S];
 #pragma unroll
-    for (int v = 0; v < 4 / VEC; ++v) pointwise_vec<T, S, false>(a, br, i0 + v * VEC);
+    for (int q = 0; q < S; ++q) d[q] = a.D[q][i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[1 + k] *= a.inv_c[k];
+    T co[ctab_pitch<T>(S)];
+    pointwise_coefs<T, S>(a, br, c, co);
+    pointwise_node<T, S>(co, c, d, g);
+#pragma unroll
+    for (int p = 0; p < S; ++p) a.D[p][i] = g[p];
   }
 }
 
 template <typename T>
 cudaError_t launch_pointwise_groups(const PointwiseArgs<T>& a, const int* list, long long count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  const long long nb = (count + 255) / 256;
+  const long long nb = (4 * count + 255) / 256;
   const unsigned grid = (unsigned)(nb < 152 * 16 ? nb : 152 * 16);
   count_launch();
   if (a.s == 4)
