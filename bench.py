@@ -170,14 +170,17 @@ def run_reference(args):
 # iteration (linear basis s = 4, w = bytes per real, u8 masks, int32 node index):
 #   x_split       p_old, r in; p, 2 fields out  (direction update fused, no input mask)
 #   y_split       2 in, 3 out
-#   z_split       3 in, s out
-#   stiff_pointwise  s in, s out, node index (irregular rows: a few % of nodes, not counted)
+#   z_split       3 in, s out (with the pointwise stage of the regular nodes when n_x % 4 == 0:
+#                 its scaled outputs are their g, plus 2 bits per 4 nodes, not counted)
+#   stiff_pointwise  s in, s out, node index: every node when n_x % 4 != 0; otherwise only
+#                 the boundary nodes the z split leaves (no per-box-node figure)
 #   z_merge       s in, 3 out
 #   y_merge       3 in, 2 out
 #   x_merge       2 in + output mask, Ap out, p in (p.Ap fused)
 #   cg_vector     x, r, p, Ap in; x, r out
-def pass_bytes(cls, w, s=4):
-    return {"x_split": 5 * w, "y_split": 5 * w, "z_split": (3 + s) * w, "stiff_pointwise": 2 * s * w + 4,
+def pass_bytes(cls, w, s=4, fused=True):
+    return {"x_split": 5 * w, "y_split": 5 * w, "z_split": (3 + s) * w,
+            "stiff_pointwise": None if fused else 2 * s * w + 4,
             "z_merge": (s + 3) * w, "y_merge": 5 * w, "x_merge": 4 * w + 1, "cg_vector": 6 * w}.get(cls)
 
 
@@ -186,15 +189,23 @@ def pass_bytes(cls, w, s=4):
 # K.u (profiles/dram_Ku_f32_cube256.md).  A value holds only while the kernel is
 # unchanged: the sha256 of each listed source region (the kernel and its
 # argument struct) is checked at run time, and the traffic is null otherwise.
+_PASSES = "paper_2403_19854_gb300/csrc/rk_passes.cuh"
+_STRIDED = (_PASSES, "template <typename T, int N, int L>\nstruct Strided {", "// PW > 0 (z SPLIT",
+            "7a4574a469839b2cdaca3f1a1c45af98b27fd3109511b5f6e8457a6417b15d14")
+_MERGE_START = ("template <typename T, int N, int L>\n__global__ void __launch_bounds__(Strided<T, N, L>::THREADS, "
+                "Strided<T, N, L>::MIN_BLOCKS_MERGE)")
 MEASURED_TRAFFIC = {
-    ("stiff_pointwise", "f32", 256): (384381952 + 212011264, [
-        ("paper_2403_19854_gb300/csrc/rk_vec.cu",
-         "template <typename T, int S>\n__global__ void __launch_bounds__(256) k_pointwise_stiff",
-         "template cudaError_t launch_pointwise_stiff<double>",
-         "e3a2afd194e7caac07baa29bfcad4eed42c24ba9188ce74e060d805fa6b6e4a8"),
-        ("paper_2403_19854_gb300/csrc/rk_internal.cuh", "struct PointwiseArgs {",
-         "cudaError_t launch_pointwise_stiff(const PointwiseArgs<T>& a, cudaStream_t s);",
-         "3b4adf934a5f9f891d469b0c982ddfc580bb2d9a59fc11b22a84becd7c62462b"),
+    ("z_split", "f32", 256): (203780352 + 230969856, [
+        _STRIDED,
+        (_PASSES, "// PW > 0 (z SPLIT", _MERGE_START,
+         "ac8f98c3b1ae4dade0e4ffc9f7ba8f82f8dd4b3c2c92ad32eca24921689a8a02"),
+        ("paper_2403_19854_gb300/csrc/rk_pointwise.cuh", "// rk_pointwise.cuh", "}  // namespace rk",
+         "a257f5466aa7c9ea768452e021edb6b696f07ef043c6416cbc057d30cca10877"),
+    ]),
+    ("z_merge", "f32", 256): (268492544 + 152822016, [
+        _STRIDED,
+        (_PASSES, _MERGE_START, "// ------------------------------------------------------------------- x passes",
+         "ed2892cc26badc1fa71f36903b97f8c638c1b366febd3bf05cff16e0ed367043"),
     ]),
 }
 
@@ -305,7 +316,7 @@ def run_ours(args):
     (dname, dprec), (dms, dn) = dom
     w = 8 if dprec == "f64" else 4
     peak, peak_kind = _peaks()
-    bpn = pass_bytes(dname, w)
+    bpn = pass_bytes(dname, w, fused=p.n[0] % 4 == 0)
     roofline = None
     if bpn is not None:
         traffic = args.traffic_bytes if args.traffic_bytes > 0 else measured_traffic(dname, dprec, args.size)

@@ -302,10 +302,10 @@ rk_status rk_solve_vjp(rk_handle* h, const double* u_bar, double* r_bar, double*
 enum {
   RK_PROF_X_SPLIT = 0,       /* x pass, forward chain (and set-up moments) */
   RK_PROF_Y_SPLIT = 1,       /* y pass, forward chain */
-  RK_PROF_Z_SPLIT = 2,       /* z pass, forward chain (set-up moments; Alg. 2 when n_x is odd) */
-  RK_PROF_Z_STIFF = 3,       /* z pass of Alg. 2 with the pointwise stage (Eq. 90-91) applied to
-                                each tile it writes; the stand-alone pointwise kernel when n_x is
-                                not a multiple of the 16-byte vector width */
+  RK_PROF_Z_SPLIT = 2,       /* z pass, forward chain (set-up moments; in Alg. 2 it also applies
+                                the pointwise stage to the regular nodes when n_x % 4 == 0) */
+  RK_PROF_Z_STIFF = 3,       /* pointwise stage of Alg. 2 (Eq. 90-91): the boundary nodes left by
+                                the z pass, or every node when n_x % 4 != 0 */
   RK_PROF_Z_EVAL_U = 4,      /* fused z pass of Alg. 3 */
   RK_PROF_Z_TRANSPOSE_U = 5, /* fused z pass of Alg. 4 / transpose of Alg. 3 */
   RK_PROF_Y_MERGE = 6,       /* y pass, reflected chain */

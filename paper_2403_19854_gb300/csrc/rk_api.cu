@@ -371,14 +371,11 @@ bool tile_maps_for(rk_handle* h, int axis, const PassArgs<T>& a, TileMaps* tm) {
   return true;
 }
 
-// pw: the z SPLIT of Alg. 2 also applies the pointwise stage (profiled as such)
+// pw: the z SPLIT of Alg. 2 also applies the pointwise stage to the regular nodes
 template <typename T>
 rk_status run_split(rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s,
                     const PointwiseArgs<T>* pw = nullptr) {
-  ProfScope ps(h,
-               prof_cls<T>(pw ? RK_PROF_Z_STIFF
-                              : (axis == 0 ? RK_PROF_X_SPLIT : (axis == 1 ? RK_PROF_Y_SPLIT : RK_PROF_Z_SPLIT))),
-               s);
+  ProfScope ps(h, prof_cls<T>(axis == 0 ? RK_PROF_X_SPLIT : (axis == 1 ? RK_PROF_Y_SPLIT : RK_PROF_Z_SPLIT)), s);
   TileMaps tm;
   const bool use = tile_maps_for<T>(h, axis, a, &tm);
   cudaError_t e = launch_split<T>(axis, h->n[axis], a, s, use ? &tm : nullptr, pw);
