@@ -235,10 +235,10 @@ struct TileFeed {
 
 // PW > 0 (z SPLIT of Alg. 2, PW = s, diagonal interior coefficients): the
 // multiplier rows of D_x, D_y, D_z carry c_k, so at regular nodes the pass writes
-// g_x, g_y, g_z of Eq. 91 directly; once a tile is written the block sets the
-// other g_p of its regular 4-node groups, and every g_p of its groups outside chi,
-// to 0.  The remaining groups (boundary layers) are left to k_pointwise_groups.
-// Requires n_x to be a multiple of 4.
+// g_x, g_y, g_z of Eq. 91 directly; it writes 0 for the other g_p of its regular
+// 4-node groups and for every g_p of its groups outside chi (flags: a bit per
+// group in pw.regbits / pw.outbits).  The remaining groups (boundary layers) are
+// left to k_pointwise_groups.  Requires n_x to be a multiple of 4.
 template <typename T, int N, int L, int PW>
 __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::MIN_BLOCKS_SPLIT)
     k_strided_split(const PassArgs<T> a, const int nbx, const long long ntiles, const int a16,
@@ -272,7 +272,19 @@ __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::M
     const long long base = x0 + (tile / nbx) * a.other_stride + 2 * l;
     const bool ok = x0 + 2 * l < a.nx;
     for (int g = 0; g < a.n_groups; ++g) {
-      if (!feed.wait(a.err)) return;
+      if (!feed.wait(a.err)) return;  // (a block-wide barrier: the previous tile's flags are no longer read)
+      if (PW > 0 && g == 0) {
+        // the flag bytes of the tile rows: a row's ROW / 4 <= 8 groups start at bit
+        // g0 = (tile origin + row * line_stride) / 4 and span at most two bytes (one
+        // spare word ends the bit arrays)
+        const uint8_t* rb = reinterpret_cast<const uint8_t*>(pw.regbits);
+        const uint8_t* ob = reinterpret_cast<const uint8_t*>(pw.outbits);
+        for (int row = threadIdx.x; row < N; row += S::THREADS) {
+          const long long g0 = (base - 2 * l + row * a.line_stride) / 4;
+          rflag[row] = (uint8_t)(((unsigned)__ldg(rb + g0 / 8) | ((unsigned)__ldg(rb + g0 / 8 + 1) << 8)) >> (g0 % 8));
+          oflag[row] = (uint8_t)(((unsigned)__ldg(ob + g0 / 8) | ((unsigned)__ldg(ob + g0 / 8 + 1) << 8)) >> (g0 % 8));
+        }
+      }
 #pragma unroll
       for (int r = 0; r < S::R; ++r) v[r] = S::at(feed.tile, F::nat_pos(t, r), l);
       RK_SYNC();  // the tile is free: fetch the next field (or the first of the next tile)
@@ -286,39 +298,18 @@ __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::M
 #pragma unroll
         for (int r = 0; r < S::R; ++r) w[r] = spec_mul(v[r], coef, N, m, F::spec_idx(t, r), a.reflect);
         F::inverse(w, t, buf, tw);
-        T* out = a.out[a.term_io[q]];
+        const int p = a.term_io[q];
+        T* out = a.out[p];
+        // g_p = 0: every p outside chi; at regular nodes every p but x, y, z (the
+        // node pair of this thread lies in group l / 2 of its tile row)
+        const bool nongrad = p < 1 || p > 3;
         if (ok)
 #pragma unroll
-          for (int r = 0; r < S::R; ++r) S::store(out, base + F::nat_pos(t, r) * a.line_stride, w[r]);
-      }
-    }
-    if (PW > 0) {
-      constexpr int VEC = 16 / sizeof(T);
-      constexpr int VPR = S::ROW / VEC;  // vectors per tile row
-      constexpr int SP = PW > 0 ? PW : 1;
-      const int nv = min(S::ROW, a.nx - x0) / VEC;
-      const long long tb = x0 + (tile / nbx) * a.other_stride;
-      // a row's ROW / 4 <= 8 groups start at bit g0 = (tb + row * line_stride) / 4
-      // and span at most two bytes of the bit arrays (one spare word at their end)
-      const uint8_t* rb = reinterpret_cast<const uint8_t*>(pw.regbits);
-      const uint8_t* ob = reinterpret_cast<const uint8_t*>(pw.outbits);
-      for (int row = threadIdx.x; row < N; row += S::THREADS) {
-        const long long g0 = (tb + row * a.line_stride) / 4;
-        const unsigned r2 = (unsigned)__ldg(rb + g0 / 8) | ((unsigned)__ldg(rb + g0 / 8 + 1) << 8);
-        const unsigned o2 = (unsigned)__ldg(ob + g0 / 8) | ((unsigned)__ldg(ob + g0 / 8 + 1) << 8);
-        rflag[row] = (uint8_t)(r2 >> (g0 % 8));
-        oflag[row] = (uint8_t)(o2 >> (g0 % 8));
-      }
-      RK_SYNC();  // the flags are in place (and every D_p of the tile is written)
-      for (int j = threadIdx.x; j < N * VPR; j += S::THREADS) {
-        const int row = j / VPR, c = j % VPR;
-        if (c >= nv) continue;
-        const long long i0 = tb + row * a.line_stride + c * VEC;
-        const int bit = c * VEC / 4;
-        if ((rflag[row] >> bit) & 1u)
-          pointwise_vec_regular<T, SP>(pw, i0);
-        else if ((oflag[row] >> bit) & 1u)
-          pointwise_vec_zero<T, SP>(pw, i0);
+          for (int r = 0; r < S::R; ++r) {
+            const int row = F::nat_pos(t, r);
+            const bool zero = PW > 0 && (((oflag[row] | (nongrad ? rflag[row] : 0)) >> (l / 2)) & 1u);
+            S::store(out, base + row * a.line_stride, zero ? cmk((T)0, (T)0) : w[r]);
+          }
       }
     }
   }

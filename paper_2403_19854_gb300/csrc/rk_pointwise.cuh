@@ -49,18 +49,6 @@ RK_DEV void pointwise_stage_breg(const PointwiseArgs<T>& a, T* br, int tid, int 
   for (int j = tid; j < CP; j += nthreads) br[j] = j < NC ? a.breg[j] : (T)0;
 }
 
-// With a.diag, a vector of regular nodes only needs g_p = 0 written for p outside
-// {x, y, z} (its g_x, g_y, g_z are the scaled D_x, D_y, D_z already).
-template <typename T, int S>
-RK_DEV void pointwise_vec_regular(const PointwiseArgs<T>& a, long long i0) {
-  using V16 = Vec16<T>;
-  V16 zero;
-  memset(&zero, 0, 16);
-#pragma unroll
-  for (int p = 0; p < S; ++p)
-    if (p < 1 || p > 3) *reinterpret_cast<V16*>(a.D[p] + i0) = zero;
-}
-
 // The 3s+1 (padded) coefficients of a node of class c: its row of the table of
 // irregular nodes (c > 0) or the shared interior values (16-byte loads).
 template <typename T, int S>
@@ -95,16 +83,6 @@ RK_DEV void pointwise_node(const T* co, int c, const T* d, T* g) {
   const T cv = c >= 0 ? co[3 * S] : (T)0;  // chi V; 0 outside chi
 #pragma unroll
   for (int p = 0; p < S; ++p) g[p] = cv * (co[p] * A[0] + co[S + p] * A[1] + co[2 * S + p] * A[2]);
-}
-
-// Nodes outside chi: g_p = 0 for every p.
-template <typename T, int S>
-RK_DEV void pointwise_vec_zero(const PointwiseArgs<T>& a, long long i0) {
-  using V16 = Vec16<T>;
-  V16 zero;
-  memset(&zero, 0, 16);
-#pragma unroll
-  for (int p = 0; p < S; ++p) *reinterpret_cast<V16*>(a.D[p] + i0) = zero;
 }
 
 // Nodes i0 .. i0 + VEC - 1, i0 a multiple of VEC = 16 / sizeof(T).  L2ONLY: the D

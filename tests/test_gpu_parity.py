@@ -230,3 +230,29 @@ def test_singular_moment_reported():
     H = rk.Handle((16, 16, 16), (0.1, 0.1, 0.1), tdev(chi), tdev(np.zeros_like(chi)), tdev(V), 1, 2.0)
     assert H.setup_status == 4
     assert H.singular == (1, 5 + 16 * (5 + 16 * 5))
+
+
+# Support sweep with the shapes of Tab. 4-5: a 20^3-node cube domain (box side
+# 20 + floor(a~), Eq. 64-67) for a~ = 1.5 ... 4.5, i.e. M = 27 ... 729 neighbours,
+# embedded in a 32^3 box; both bases where the moment matrices are regular.
+@pytest.mark.parametrize("a,deg", [(1.5, 1), (2.0, 1), (2.5, 1), (3.0, 1), (3.5, 1), (4.0, 1), (4.5, 1),
+                                   (2.5, 2), (3.5, 2), (4.5, 2)])
+def test_support_sweep_tab4_tab5(a, deg):
+    nb = 20 + int(np.floor(a))
+    p = W.embed(W.cube_problem(nb, a, deg, "zero"), (32, 32, 32))
+    assert int(p.chi.sum()) == 20 ** 3
+    H = rk.Handle.from_problem(p, device=DEV)
+    o = Oracle(p.n, p.h, a, deg, p.chi)
+    m = p.chi > 0
+    bg = np_(H.get_b(torch.empty(4 * p.s * p.nbox, dtype=torch.float64, device=DEV)))
+    bo = o.b_fields()
+    for i in range(4):
+        assert rel(bg[i][:, m], bo[i][:, m]) < TOL64, f"b family {i}"
+    d = W.random_field(p.nbox, 13)
+    fo = o.apply_K(p.V, d * p.chi)
+    f = np_(H.apply_K(tdev(d)))
+    assert rel(f, fo, m) < TOL64
+    assert np.all(f[~m] == 0.0)
+    f32 = np_(H.apply_K(tdev(d.astype(np.float32)))).astype(np.float64)
+    assert rel(f32, o.apply_K(p.V, d.astype(np.float32).astype(np.float64) * p.chi), m) < TOL32
+    H.close()
