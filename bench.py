@@ -195,14 +195,14 @@ _STRIDED = (_PASSES, "template <typename T, int N, int L>\nstruct Strided {", "/
 _MERGE_START = ("template <typename T, int N, int L>\n__global__ void __launch_bounds__(Strided<T, N, L>::THREADS, "
                 "Strided<T, N, L>::MIN_BLOCKS_MERGE)")
 MEASURED_TRAFFIC = {
-    ("z_split", "f32", 256): (203780352 + 230969856, [
+    ("z_split", "f32", 256): (202878208 + 210755328, [
         _STRIDED,
         (_PASSES, "// PW > 0 (z SPLIT", _MERGE_START,
-         "ac8f98c3b1ae4dade0e4ffc9f7ba8f82f8dd4b3c2c92ad32eca24921689a8a02"),
+         "d5e51b6bc7d7509197db15a71b69eb846cdd73cf477f7041bafff3a4179309f8"),
         ("paper_2403_19854_gb300/csrc/rk_pointwise.cuh", "// rk_pointwise.cuh", "}  // namespace rk",
-         "a257f5466aa7c9ea768452e021edb6b696f07ef043c6416cbc057d30cca10877"),
+         "9bbfd8b1f836022992c4b6b4ea5a93dc93f98c10454a65cfd19c154923b3e842"),
     ]),
-    ("z_merge", "f32", 256): (268492544 + 152822016, [
+    ("z_merge", "f32", 256): (268490240 + 152869376, [
         _STRIDED,
         (_PASSES, _MERGE_START, "// ------------------------------------------------------------------- x passes",
          "ed2892cc26badc1fa71f36903b97f8c638c1b366febd3bf05cff16e0ed367043"),
