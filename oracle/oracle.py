@@ -66,6 +66,13 @@ def _load():
     lib.orc_nslot.argtypes = [ctypes.c_void_p]
     lib.orc_reach.restype = ctypes.c_int
     lib.orc_reach.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    for name in ("orc_s", "orc_dim"):
+        getattr(lib, name).restype = ctypes.c_int
+        getattr(lib, name).argtypes = [ctypes.c_void_p]
+    lib.orc_grid_dim.restype = ctypes.c_int
+    lib.orc_grid_dim.argtypes = [_intp]
+    lib.orc_basis_size_dim.restype = ctypes.c_int
+    lib.orc_basis_size_dim.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.orc_node_box.argtypes = [ctypes.c_void_p, _i64p]
     lib.orc_shape_tables.argtypes = [ctypes.c_void_p, _i64p, _f64p, _f64p]
     lib.orc_neighbour_count.restype = ctypes.c_int
@@ -118,7 +125,10 @@ class Oracle:
     """Traditional RKPM discretisation of one domain (chi nodes of a grid).
 
     n: (nx, ny, nz) grid points; h: (hx, hy, hz) spacing; a_tilde: support in
-    units of h (Eq. 64); degree: 1 (s = 4) or 2 (s = 10); chi: grid-indexed 0/1.
+    units of h (Eq. 64); degree: 1 or 2; chi: grid-indexed 0/1.  A grid with
+    nz = 1 is two-dimensional and one with ny = nz = 1 one-dimensional: the
+    absent axes carry no kernel factor, monomial or gradient (s = 4 / 10 in 3D,
+    3 / 6 in 2D, 2 / 3 in 1D; b^k = 0 on an absent axis).
     """
 
     def __init__(self, n, h, a_tilde, degree, chi):
@@ -127,14 +137,17 @@ class Oracle:
         self.h = tuple(float(v) for v in h)
         self.a_tilde = float(a_tilde)
         self.degree = int(degree)
-        self.s = 4 if degree == 1 else 10
         self.nbox = self.n[0] * self.n[1] * self.n[2]
         self._chi, pchi = _u8(np.asarray(chi).reshape(-1))
         nn = (ctypes.c_int * 3)(*self.n)
         hh = (ctypes.c_double * 3)(*self.h)
+        if lib.orc_grid_dim(nn) < 0 or self.degree not in (1, 2):
+            raise ValueError("oracle: grid must be (n, 1, 1), (n, m, 1) or (n, m, l) with n > 1; degree 1 or 2")
         self._h = lib.orc_create(nn, hh, self.a_tilde, self.degree, pchi)
         if not self._h:
             raise MemoryError("oracle: allocation failed")
+        self.s = lib.orc_s(self._h)
+        self.dim = lib.orc_dim(self._h)
         self.nnode = lib.orc_nnode(self._h)
         self.nslot = lib.orc_nslot(self._h)
         self.reach = tuple(lib.orc_reach(self._h, k) for k in range(3))
@@ -309,7 +322,10 @@ def apply_K_sampled(n, h, a_tilde, degree, chi, V, d, sample) -> np.ndarray:
 def b_sampled(n, h, a_tilde, degree, chi, sample) -> np.ndarray:
     """(nsample, 4, s) correction coefficients at the given grid points."""
     lib = _load()
-    s = 4 if degree == 1 else 10
+    nn = (ctypes.c_int * 3)(*[int(v) for v in n])
+    s = lib.orc_basis_size_dim(int(degree), lib.orc_grid_dim(nn))
+    if s < 0:
+        raise ValueError("oracle: bad grid or degree")
     chi, pchi = _u8(np.asarray(chi).reshape(-1))
     sample, ps = _i64(np.asarray(sample).reshape(-1))
     out = np.zeros((sample.size, 4, s))

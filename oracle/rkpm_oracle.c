@@ -1,6 +1,7 @@
 /*
- * rkpm_oracle.c -- traditional (neighbour-loop) RKPM for the 3D Poisson problem,
- * in FP64 on the CPU.
+ * rkpm_oracle.c -- traditional (neighbour-loop) RKPM for the Poisson problem in
+ * 3D (and, on grids with trailing axes of one point, in 2D and 1D: Sec. 6.1), in
+ * FP64 on the CPU.
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the GPU path is checked
  * against.  Only the tests, the smoke check and the CPU-baseline leg of the
@@ -27,7 +28,8 @@
  *    b^0 = first row of M_s^{-1} and b^k = -(1/a_k) * row (1+k) of M_s^{-1}
  *    (Eq. 45-47 rewritten for the scaled basis).
  *  - Basis ordering (Eq. 4 extended to 3D): [1, x, y, z] for n = 1 and
- *    [1, x, y, z, x^2, xy, xz, y^2, yz, z^2] for n = 2.
+ *    [1, x, y, z, x^2, xy, xz, y^2, yz, z^2] for n = 2; in 2D and 1D the entries
+ *    that involve only the present coordinates, in the same order.
  *
  * Parity pins: see the oracle tests (reproducing conditions, closed-form
  * interior stencil at a = 2h, neighbour counts of Tab. 4-5, K symmetry,
@@ -56,20 +58,26 @@ double orc_phi1(double z) {
 /* Eq. 5: number of monomials of degree <= n in 3D. */
 int orc_basis_size(int degree) { return degree == 1 ? 4 : (degree == 2 ? 10 : -1); }
 
-/* Eq. 4 in 3D, scaled argument xi = (x - x_I)/a. */
-static void basis(int degree, const double xi[3], double *H) {
-  H[0] = 1.0;
-  H[1] = xi[0];
-  H[2] = xi[1];
-  H[3] = xi[2];
-  if (degree == 2) {
-    H[4] = xi[0] * xi[0];
-    H[5] = xi[0] * xi[1];
-    H[6] = xi[0] * xi[2];
-    H[7] = xi[1] * xi[1];
-    H[8] = xi[1] * xi[2];
-    H[9] = xi[2] * xi[2];
-  }
+/* The same in dim = 1, 2, 3 dimensions: (n + dim)! / (n! dim!). */
+int orc_basis_size_dim(int degree, int dim) {
+  if (degree != 1 && degree != 2) return -1;
+  if (dim == 1) return degree + 1;
+  if (dim == 2) return degree == 1 ? 3 : 6;
+  if (dim == 3) return orc_basis_size(degree);
+  return -1;
+}
+
+/* Eq. 4, scaled argument xi = (x - x_I)/a, in dim dimensions.  The paper states
+   the method in 2D and obtains 1D and 3D by dropping or adding a coordinate, so
+   the monomials are those of the 3D list [1, x, y, z, x^2, xy, xz, y^2, yz, z^2]
+   that involve only the first dim coordinates, in that order. */
+static void basis(int degree, int dim, const double xi[3], double *H) {
+  int q = 0;
+  H[q++] = 1.0;
+  for (int k = 0; k < dim; ++k) H[q++] = xi[k];
+  if (degree == 2)
+    for (int k = 0; k < dim; ++k)
+      for (int l = k; l < dim; ++l) H[q++] = xi[k] * xi[l];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -80,6 +88,7 @@ typedef struct {
   int n[3];
   double h[3];
   double a[3];     /* support size per axis, Eq. 64: a_k = a_tilde * h_k */
+  int dim;         /* axes with n[k] > 1; the others (trailing) are absent */
   int degree, s;
   int r[3];        /* reach: largest |offset| with phi1 > 0 on that axis */
   int w[3];        /* 2r+1 */
@@ -97,10 +106,20 @@ static void gcoord(const geom_t *g, int64_t idx, int c[3]) {
   c[2] = (int)(idx / ((int64_t)g->n[0] * g->n[1]));
 }
 
+/* Dimension of a grid: 3, or 2 when n[2] == 1, or 1 when n[1] == n[2] == 1
+   (absent axes are trailing); -1 otherwise. */
+int orc_grid_dim(const int n[3]) {
+  if (n[0] < 2) return -1;
+  if (n[1] == 1) return n[2] == 1 ? 1 : -1;
+  return n[2] == 1 ? 2 : 3;
+}
+
 static int geom_init(geom_t *g, const int n[3], const double h[3], double a_tilde, int degree,
                      const uint8_t *chi) {
   g->degree = degree;
-  g->s = orc_basis_size(degree);
+  g->dim = orc_grid_dim(n);
+  if (g->dim < 0) return -1;
+  g->s = orc_basis_size_dim(degree, g->dim);
   if (g->s < 0) return -1;
   g->nslot = 1;
   for (int k = 0; k < 3; ++k) {
@@ -108,7 +127,7 @@ static int geom_init(geom_t *g, const int n[3], const double h[3], double a_tild
     g->h[k] = h[k];
     g->a[k] = a_tilde * h[k];
     int r = 0;
-    while (orc_phi1(((double)(r + 1) * h[k]) / g->a[k]) > 0.0) ++r;
+    while (k < g->dim && orc_phi1(((double)(r + 1) * h[k]) / g->a[k]) > 0.0) ++r;
     g->r[k] = r;
     g->w[k] = 2 * r + 1;
     g->nslot *= g->w[k];
@@ -195,28 +214,30 @@ static int shape_at(const geom_t *g, int64_t S, double *psi, double *dpsi, doubl
         cI[2] >= g->n[2])
       continue;
     if (!g->chi[gidx(g, cI[0], cI[1], cI[2])]) continue;
-    double xi[3], ph = 1.0;
-    for (int k = 0; k < 3; ++k) {
+    double xi[3] = {0.0, 0.0, 0.0}, ph = 1.0;
+    for (int k = 0; k < g->dim; ++k) {  /* Eq. 6: product kernel over the present axes */
       double dx = (double)(cS[k] - cI[k]) * g->h[k]; /* x_S - x_I */
       xi[k] = dx / g->a[k];
       ph *= orc_phi1(fabs(dx) / g->a[k]);
     }
     if (ph == 0.0) continue;
-    basis(g->degree, xi, H);
+    basis(g->degree, g->dim, xi, H);
     for (int p = 0; p < s; ++p)
       for (int q = 0; q < s; ++q) M[p * s + q] += H[p] * H[q] * ph;
   }
   if (cholesky(s, M)) return 1;
-  /* rows 1..4 of M^{-1} (M symmetric: row i = M^{-1} e_i) */
+  /* rows 1..1+dim of M^{-1} (M symmetric: row i = M^{-1} e_i) */
   double rows[4][ORC_MAXS];
-  for (int i = 0; i < 4; ++i) {
+  memset(rows, 0, sizeof(rows));
+  for (int i = 0; i <= g->dim; ++i) {
     for (int p = 0; p < s; ++p) rows[i][p] = (p == i) ? 1.0 : 0.0;
     chol_solve(s, M, rows[i]);
   }
   double b[4][ORC_MAXS];
   for (int p = 0; p < s; ++p) {
     b[0][p] = rows[0][p];                     /* Eq. 45 */
-    for (int k = 0; k < 3; ++k) b[1 + k][p] = -rows[1 + k][p] / g->a[k]; /* Eq. 46-47 */
+    for (int k = 0; k < 3; ++k)               /* Eq. 46-47; 0 on an absent axis */
+      b[1 + k][p] = k < g->dim ? -rows[1 + k][p] / g->a[k] : 0.0;
   }
   if (bout)
     for (int i = 0; i < 4; ++i)
@@ -230,14 +251,14 @@ static int shape_at(const geom_t *g, int64_t S, double *psi, double *dpsi, doubl
         cI[2] >= g->n[2])
       continue;
     if (!g->chi[gidx(g, cI[0], cI[1], cI[2])]) continue;
-    double xi[3], ph = 1.0;
-    for (int k = 0; k < 3; ++k) {
+    double xi[3] = {0.0, 0.0, 0.0}, ph = 1.0;
+    for (int k = 0; k < g->dim; ++k) {
       double dx = (double)(cS[k] - cI[k]) * g->h[k];
       xi[k] = dx / g->a[k];
       ph *= orc_phi1(fabs(dx) / g->a[k]);
     }
     if (ph == 0.0) continue;
-    basis(g->degree, xi, H);
+    basis(g->degree, g->dim, xi, H);
     double v0 = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;
     for (int p = 0; p < s; ++p) {
       v0 += b[0][p] * H[p];
@@ -329,6 +350,8 @@ orc_ctx *orc_create(const int n[3], const double h[3], double a_tilde, int degre
 int64_t orc_nnode(const orc_ctx *c) { return c->nnode; }
 int orc_nslot(const orc_ctx *c) { return c->g.nslot; }
 int orc_reach(const orc_ctx *c, int axis) { return c->g.r[axis]; }
+int orc_s(const orc_ctx *c) { return c->g.s; }
+int orc_dim(const orc_ctx *c) { return c->g.dim; }
 int64_t orc_nsingular(const orc_ctx *c) { return c->nsingular; }
 int64_t orc_first_singular(const orc_ctx *c) { return c->first_singular; }
 
@@ -806,7 +829,7 @@ int64_t orc_b_sampled(const int n[3], const double h[3], double a_tilde, int deg
     if (!chi[sample[q]]) {
       for (int i = 0; i < 4 * g.s; ++i) o[i] = 0.0;
       o[0] = 1.0;
-      for (int k = 0; k < 3; ++k) o[(1 + k) * g.s + 1 + k] = -1.0 / g.a[k];
+      for (int k = 0; k < g.dim; ++k) o[(1 + k) * g.s + 1 + k] = -1.0 / g.a[k];
       continue;
     }
     if (shape_at(&g, sample[q], psi, dpsi, o)) ++bad;

@@ -50,8 +50,14 @@ class Problem:
         return int(self.chi.sum())
 
     @property
+    def dim(self) -> int:
+        """3, or 2 when nz = 1, or 1 when ny = nz = 1 (absent axes are trailing)."""
+        return 1 if self.n[1] == 1 and self.n[2] == 1 else (2 if self.n[2] == 1 else 3)
+
+    @property
     def s(self) -> int:
-        return 4 if self.degree == 1 else 10
+        """Monomials of degree <= n in dim coordinates (Eq. 5)."""
+        return {1: self.degree + 1, 2: 3 if self.degree == 1 else 6, 3: 4 if self.degree == 1 else 10}[self.dim]
 
     def coords(self):
         """(X, Y, Z) flat coordinate arrays of the box nodes (Eq. 71)."""
@@ -118,6 +124,53 @@ def cube_problem(n_box, a_tilde, degree=1, kind="sin", lo=0.0, hi=1.0):
     return Problem(n=(nb, nb, nb), h=(h, h, h), a_tilde=float(a_tilde), degree=int(degree), chi=chi,
                    chi_gamma=chi_gamma, V=V, r=r, g=g, u_exact=u, name=f"cube{nb}-{kind}",
                    meta={"n_omega_side": n_om, "lo": lo, "hi": hi})
+
+
+def line_problem(n_box, a_tilde=1.5, degree=1):
+    """The 1D problem of Sec. 6.1.1 (Eq. 97-98): -u'' = 2 on [-1, 1], u(-1) = u(1) = 0,
+    exact u = 1 - x^2.  A line of n_box nodes (grid (n_box, 1, 1)), of which
+    n_box - floor(a_tilde) span [-1, 1] (the box rule of Eq. 64-67); V = h, halved
+    at the two end nodes (trapezoidal share); Gamma_g = the two end nodes."""
+    nb = int(n_box)
+    n_om = domain_side(nb, a_tilde)
+    if n_om < 2:
+        raise ValueError("box too small for this support")
+    h = 2.0 / (n_om - 1)
+    x = -1.0 + np.arange(nb) * h
+    inside, face = _face_flags(nb, n_om)
+    chi = inside.astype(np.uint8)
+    chi_gamma = (inside & face).astype(np.uint8)
+    V = np.where(inside, h * np.where(face, 0.5, 1.0), 0.0)
+    u = np.where(inside, 1.0 - x ** 2, 0.0)
+    r = np.where(inside, 2.0, 0.0)
+    return Problem(n=(nb, 1, 1), h=(h, h, h), a_tilde=float(a_tilde), degree=int(degree), chi=chi,
+                   chi_gamma=chi_gamma, V=V, r=r, g=np.zeros(nb), u_exact=u, name=f"line{nb}",
+                   meta={"n_omega_side": n_om, "lo": -1.0, "hi": 1.0})
+
+
+def plane_problem(n_box, a_tilde=1.5, degree=1):
+    """The 2D problem of Sec. 6.1.2 (Eq. 101-102): -Lap u = 4 - 2x^2 - 2y^2 on
+    [-1, 1]^2, u = 0 on the boundary, exact u = (1 - x^2)(1 - y^2).  A square of
+    n_box^2 nodes (grid (n_box, n_box, 1)) with n_box - floor(a_tilde) domain nodes
+    per axis; V = h^2 halved once per axis on which a node lies on the boundary;
+    Gamma_g = the boundary nodes."""
+    nb = int(n_box)
+    n_om = domain_side(nb, a_tilde)
+    if n_om < 2:
+        raise ValueError("box too small for this support")
+    h = 2.0 / (n_om - 1)
+    inside, face = _face_flags(nb, n_om)
+    ins2 = inside[None, :] & inside[:, None]
+    fc = face[None, :].astype(np.int32) + face[:, None]
+    x1 = -1.0 + np.arange(nb) * h
+    X, Y = x1[None, :], x1[:, None]
+    u = np.where(ins2, (1 - X ** 2) * (1 - Y ** 2), 0.0).reshape(-1)
+    r = np.where(ins2, 4.0 - 2.0 * X ** 2 - 2.0 * Y ** 2, 0.0).reshape(-1)
+    V = np.where(ins2, h ** 2 * 0.5 ** fc, 0.0).reshape(-1)
+    return Problem(n=(nb, nb, 1), h=(h, h, h), a_tilde=float(a_tilde), degree=int(degree),
+                   chi=ins2.astype(np.uint8).reshape(-1), chi_gamma=(ins2 & (fc > 0)).astype(np.uint8).reshape(-1),
+                   V=V, r=r, g=np.zeros(nb * nb), u_exact=u, name=f"plane{nb}",
+                   meta={"n_omega_side": n_om, "lo": -1.0, "hi": 1.0})
 
 
 def boundary_of(chi3: np.ndarray) -> np.ndarray:

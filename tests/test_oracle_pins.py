@@ -416,3 +416,92 @@ def test_mass_terms_appendix_c():
     assert abs(ml.sum() - p.V.sum()) <= 1e-13 * p.V.sum()
     X, _, _ = p.coords()
     assert abs(M(X * m).sum() - np.sum(p.V * X)) <= 1e-13 * np.sum(np.abs(p.V * X))
+
+
+# ----------------------------------------------------------- 1D and 2D (Sec. 6.1)
+def _monomials_dim(deg, dim):
+    """Exponent triples of the degree <= deg monomials in the first dim coordinates."""
+    return [al for al in _monomials(deg) if all(al[k] == 0 for k in range(dim, 3))]
+
+
+@pytest.mark.parametrize("dim,deg,a", [(1, 1, 1.5), (1, 2, 2.5), (2, 1, 1.5), (2, 2, 2.5)])
+def test_reproducing_conditions_1d_2d(dim, deg, a):
+    """The reproducing conditions of Eq. 2-3 and 15-16 on the 1D and 2D grids of
+    Sec. 6.1.1-6.1.2 (the paper states the method in 2D; 1D drops a coordinate):
+    monomials of the present coordinates are reproduced, and the gradient along an
+    absent axis is 0.  A basis that kept an absent coordinate would make M singular."""
+    p = W.line_problem(24, a, deg) if dim == 1 else W.plane_problem(14, a, deg)
+    o = Oracle(p.n, p.h, a, deg, p.chi)
+    assert o.dim == dim and o.s == p.s and o.nsingular == 0
+    nbr, psi, dpsi = o.shape_tables()
+    nb = o.node_box()
+    X = _coords(p)
+    valid = nbr >= 0
+    rel = (X[nb[np.where(valid, nbr, 0)]] - X[nb][:, None, :]) / (a * np.asarray(p.h))
+    hh = np.asarray(p.h)
+    for al in _monomials_dim(deg, dim):
+        mono = np.where(valid, rel[..., 0] ** al[0] * rel[..., 1] ** al[1] * rel[..., 2] ** al[2], 0.0)
+        assert np.abs((psi * mono).sum(1) - (1.0 if al == (0, 0, 0) else 0.0)).max() < 1e-12
+        for k in range(3):
+            t = 1.0 if (k < dim and al == tuple(1 if j == k else 0 for j in range(3))) else 0.0
+            assert np.abs((dpsi[..., k] * mono).sum(1) * a * hh[k] - t).max() < 1e-11
+    assert np.all(dpsi[..., dim:] == 0.0)
+
+
+def test_interior_stiffness_row_1d_a2():
+    """1D at a = 2h: the interior moment matrix is diag(1, 1/12) in the scaled basis, so
+    Psi^grad_{S+o}(x_S) = 3 o w_o / h with w = (1/6, 2/3, 1/6): the central difference
+    (d_{S+1} - d_{S-1}) / (2h).  With V = h (Eq. 54) a deep-interior row of K is
+    [-1/(4h), 0, 1/(2h), 0, -1/(4h)] at offsets -2 .. 2 (the checkerboard null mode
+    of DNI that the paper notes)."""
+    p = W.line_problem(32, 2.0, 1)
+    o = Oracle(p.n, p.h, 2.0, 1, p.chi)
+    h = p.h[0]
+    nbr, psi, dpsi = o.shape_tables()
+    nb = o.node_box()
+    S = int(np.searchsorted(nb, 12))
+    for sl, off in enumerate((-1, 0, 1)):
+        assert psi[S, sl] == pytest.approx(float(_w_a2()[off]), abs=1e-15)
+        assert dpsi[S, sl, 0] * 2 * h == pytest.approx(float(off), abs=1e-13)
+    o.assemble_K(p.V)
+    ptr, col, val = o.K_csr()
+    I = int(np.searchsorted(nb, 12))
+    row = {int(nb[col[e]]) - 12: val[e] for e in range(ptr[I], ptr[I + 1])}
+    exact = {-2: -0.25 / h, -1: 0.0, 0: 0.5 / h, 1: 0.0, 2: -0.25 / h}
+    for D, v in exact.items():
+        assert row.get(D, 0.0) == pytest.approx(v, rel=1e-12, abs=1e-12 / h)
+    assert set(row) <= set(exact)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_stiffness_symmetric_constants_in_null_space_1d_2d(dim):
+    """K of Eq. 50 is symmetric and annihilates constants (gradient reproduction)."""
+    p = W.line_problem(24, 2.5, 1) if dim == 1 else W.plane_problem(16, 2.5, 1)
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    o.assemble_K(p.V)
+    ptr, col, val = o.K_csr()
+    import scipy.sparse as sp
+    K = sp.csr_matrix((val, col, ptr), shape=(o.nnode, o.nnode))
+    nK = abs(K).max()
+    assert abs(K - K.T).max() <= 1e-14 * nK
+    assert np.abs(K @ np.ones(o.nnode)).max() <= 1e-13 * nK
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_manufactured_solution_quadratic_rate_1d_2d(dim):
+    """Sec. 6.1.1 (Eq. 97-99) and Sec. 6.1.2 (Eq. 101-103): a = 1.5h, linear basis; the
+    paper reports quadratic convergence (Fig. 9, Fig. 11).  Nodal normalised L2 error
+    of Eq. 104."""
+    sizes = (16, 32, 64, 128) if dim == 1 else (12, 16, 24, 32)
+    errs, hs = [], []
+    for nb in sizes:
+        p = W.line_problem(nb, 1.5, 1) if dim == 1 else W.plane_problem(nb, 1.5, 1)
+        o = Oracle(p.n, p.h, 1.5, 1, p.chi)
+        d, info = o.solve(p.V, p.chi_gamma, p.r, p.g, tol=1e-13)
+        assert info["converged"]
+        m = p.chi > 0
+        u = o.eval_u(d)
+        errs.append(np.sqrt(((u - p.u_exact)[m] ** 2).sum() / (p.u_exact[m] ** 2).sum()))
+        hs.append(p.h[0])
+    rates = np.diff(np.log(errs)) / np.diff(np.log(hs))
+    assert np.all(rates > 1.9) and np.all(rates < 2.1)
