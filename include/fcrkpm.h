@@ -126,7 +126,10 @@ int rk_supported_length(int n);
  * chi o F^-1[F(chi) o F(H_p o H^a_q)] (Eq. 80) in FP64, solves the s x s system
  * at every node (FP64 Cholesky) and stores b^0, b^x, b^y, b^z (Eq. 83-85) in FP64
  * and FP32, plus chi*V (Eq. 87).
- *   grid       box size and spacing
+ *   grid       box size and spacing; n[2] == 1 makes the problem two-dimensional
+ *              (Sec. 6.1.2: no z axis, kernel phi(x)phi(y), basis [1, x, y] or
+ *              [1, x, y, x^2, xy, y^2], b^z = 0, V the 2D cell measure); n[1] == 1
+ *              (1D) is not built
  *   chi        uint8[nbox], Eq. 40
  *   chi_gamma  uint8[nbox], Eq. 95 (NULL: no Dirichlet nodes)
  *   V          double[nbox], nodal volumes of direct nodal integration (Eq. 54, 87)
@@ -135,7 +138,7 @@ int rk_supported_length(int n);
  *   stream     cudaStream_t for the set-up work (synchronised before return)
  *   out        receives the handle
  * Errors: RK_ERR_INVALID_ARG, RK_ERR_UNSUPPORTED (size not built, odd sizes, gap
- * narrower than Eq. 66), RK_ERR_OOM, RK_ERR_CUDA, RK_ERR_SINGULAR_MOMENT (the
+ * narrower than Eq. 66, 1D grid), RK_ERR_OOM, RK_ERR_CUDA, RK_ERR_SINGULAR_MOMENT (the
  * handle is still returned; rk_singular_nodes gives the count and first node).
  */
 rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_gamma, const double* V,
@@ -164,8 +167,8 @@ rk_status rk_apply_K(rk_handle* h, const void* d, void* f, int32_t dtype, void* 
  * shift = 1e-3 lam(2 pi / n_x, 0, 0), which keeps the constant mode invertible.  M^{-1}
  * is symmetric positive definite on chi_Omega, as PCG requires.
  * r, z: box arrays (x fastest) of dtype RK_F64 or RK_F32, host or device.
- * Errors: RK_ERR_UNSUPPORTED when the domain has no regular node or a box side
- * exceeds 256.
+ * Errors: RK_ERR_UNSUPPORTED when the domain has no regular node, a box side
+ * exceeds 256, or the box is two-dimensional.
  */
 rk_status rk_apply_precond(rk_handle* h, const void* r, void* z, int32_t dtype, void* stream);
 

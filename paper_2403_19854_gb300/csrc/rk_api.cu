@@ -66,13 +66,20 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Monomial exponents of the basis (Eq. 4 in 3D), graded order.
-void basis_exponents(int degree, int alpha[][3]) {
+// Monomial exponents of the basis (Eq. 4 in 3D), graded order; in 2D (dim = 2) the
+// monomials free of z, in the same order ([1, x, y] / [1, x, y, x^2, xy, y^2]: the
+// paper states the method in 2D).  Returns s.
+int basis_exponents(int degree, int dim, int alpha[][3]) {
   static const int e[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
                                {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
-  const int s = degree == 1 ? 4 : 10;
-  for (int p = 0; p < s; ++p)
-    for (int k = 0; k < 3; ++k) alpha[p][k] = e[p][k];
+  const int n3 = degree == 1 ? 4 : 10;
+  int s = 0;
+  for (int p = 0; p < n3; ++p) {
+    if (dim < 3 && e[p][2] != 0) continue;
+    for (int k = 0; k < 3; ++k) alpha[s][k] = e[p][k];
+    ++s;
+  }
+  return s;
 }
 
 // Structure of the forward / reflected chains for the basis of the handle:
@@ -84,10 +91,9 @@ struct Chain {
   int nY = 0;
   int ymx[kMaxIn], ymy[kMaxIn];
   std::vector<std::pair<int, int>> zterms[kMaxIn];  // (m_z, p)
-  void build(int degree) {
+  void build(int degree, int dim) {
     deg = degree;
-    s = degree == 1 ? 4 : 10;
-    basis_exponents(degree, alpha);
+    s = basis_exponents(degree, dim, alpha);
     nX = deg + 1;
     nY = 0;
     for (int p = 0; p < s; ++p) {
@@ -110,6 +116,7 @@ struct Chain {
 // --------------------------------------------------------------------- handle
 struct rk_handle {
   int n[3];
+  int dim = 3;  // 2 when n[2] == 1: no z axis (no z kernel factor, monomial or gradient)
   double h[3];
   double a_tilde;
   int degree, s;
@@ -446,10 +453,13 @@ rk_status chain_forward_xy(rk_handle* h, const T* d, const uint8_t* in_mask, cud
 }
 
 // reflected chain, y and x passes: f = out_mask o sum conv_x(Hbar) conv_y(Hbar) G   (Alg. 2 last line)
+// G_g in workspace field gin + g (default: the z-pass outputs; in 2D the fields of
+// the y-pass outputs, which hold g_p there)
 template <typename T>
 rk_status chain_reflect_yx(rk_handle* h, T* f, const uint8_t* out_mask, cudaStream_t s,
-                           const CGFuse<T>* fuse = nullptr) {
+                           const CGFuse<T>* fuse = nullptr, int gin = -1) {
   const Chain& c = h->chain;
+  if (gin < 0) gin = c.nX + c.nY;
   PassArgs<T> ay = pass_base<T>(h, 1);
   ay.reflect = 1;
   ay.n_groups = c.nX;
@@ -460,7 +470,7 @@ rk_status chain_reflect_yx(rk_handle* h, T* f, const uint8_t* out_mask, cudaStre
     ay.g_begin[mx] = q;
     for (int g = 0; g < c.nY; ++g)
       if (c.ymx[g] == mx) {
-        ay.in[g] = h->ws<T>(c.nX + c.nY + g);
+        ay.in[g] = h->ws<T>(gin + g);
         ay.term_io[q] = g;
         ay.term_m[q] = c.ymy[g];
         ++q;
@@ -527,11 +537,44 @@ rk_status run_z(rk_handle* h, int mode, const ZArgs<T>& a, cudaStream_t s) {
 // Alg. 2: f = out_mask o K (in_mask o d).  The z axis runs as three kernels: a
 // SPLIT along z (E_(ax,ay) -> D_p, p = 1..s), the pointwise stage of Eq. 90-91 in
 // place (D_p -> g_p), and a reflected MERGE along z (g_p -> G_(ax,ay)).
+// p -> workspace field of D_p in 2D: the y-pass output of the group of p (each
+// group (m_x, m_y) holds one basis function there)
+inline int field_2d(const Chain& c, int p) {
+  for (int g = 0; g < c.nY; ++g)
+    if (c.zterms[g][0].second == p) return c.nX + g;
+  return -1;
+}
+
+template <typename T>
+PointwiseArgs<T> pointwise_base(const rk_handle* h) {
+  PointwiseArgs<T> pw;
+  memset(&pw, 0, sizeof(pw));
+  pw.s = h->s;
+  pw.cidx = h->cidx;
+  pw.ctab = ctab_of<T>(h);
+  pw.n_irr = h->n_irr;
+  for (int j = 0; j < 3 * h->s + 1; ++j) pw.breg[j] = breg_of<T>(h, j);
+  pw.nbox = h->nbox;
+  return pw;
+}
+
 template <typename T>
 rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uint8_t* out_mask, cudaStream_t s,
                const CGFuse<T>* fuse = nullptr) {
   const Chain& c = h->chain;
   RK_TRY(chain_forward_xy<T>(h, d, in_mask, s, fuse));
+  if (h->dim == 2) {
+    // no z axis: the y outputs are the D_p; the pointwise stage in place, then the
+    // reflected y and x passes read the g_p from the same fields
+    PointwiseArgs<T> pw = pointwise_base<T>(h);
+    for (int p = 0; p < h->s; ++p) pw.D[p] = h->ws<T>(field_2d(c, p));
+    {
+      ProfScope ps(h, prof_cls<T>(RK_PROF_Z_STIFF), s);
+      cudaError_t e = launch_pointwise_stiff<T>(pw, s);
+      if (e != cudaSuccess) return cuda_fail(e, "pointwise stage");
+    }
+    return chain_reflect_yx<T>(h, f, out_mask, s, fuse, c.nX);
+  }
   const int dbase = c.nX + 2 * c.nY;  // D_p / g_p fields
   PassArgs<T> az = pass_base<T>(h, 2);
   az.n_groups = c.nY;
@@ -603,6 +646,13 @@ rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uin
 template <typename T>
 rk_status op_U(rk_handle* h, const T* d, T* u, cudaStream_t s) {
   RK_TRY(chain_forward_xy<T>(h, d, h->chi, s));
+  if (h->dim == 2) {
+    T* D[10];
+    for (int p = 0; p < h->s; ++p) D[p] = h->ws<T>(field_2d(h->chain, p));
+    ProfScope ps(h, prof_cls<T>(RK_PROF_Z_EVAL_U), s);
+    cudaError_t e = launch_eval_u_fields<T>(u, D, bfields<T>(h), h->s, h->chi, h->nbox, s);
+    return e == cudaSuccess ? RK_OK : cuda_fail(e, "u^h");
+  }
   ZArgs<T> z = z_base<T>(h);
   for (int g = 0; g < h->chain.nY; ++g) z.in[g] = h->ws<T>(h->chain.nX + g);
   z.out1 = u;
@@ -614,6 +664,16 @@ rk_status op_U(rk_handle* h, const T* d, T* u, cudaStream_t s) {
 // w = chi o sum_p conv(weight o b^0_p o y, Hbar^a_p)
 template <typename T>
 rk_status op_UT(rk_handle* h, const T* y, T* w, const T* wfield, const uint8_t* wmask, cudaStream_t s) {
+  if (h->dim == 2) {
+    T* D[10];
+    for (int p = 0; p < h->s; ++p) D[p] = h->ws<T>(field_2d(h->chain, p));
+    {
+      ProfScope ps(h, prof_cls<T>(RK_PROF_Z_TRANSPOSE_U), s);
+      cudaError_t e = launch_transpose_u_fields<T>(D, y, bfields<T>(h), h->s, wfield, wmask, h->nbox, s);
+      if (e != cudaSuccess) return cuda_fail(e, "transpose of u^h");
+    }
+    return chain_reflect_yx<T>(h, w, h->chi, s, nullptr, h->chain.nX);
+  }
   ZArgs<T> z = z_base<T>(h);
   z.in1 = y;
   z.wfield = wfield;
@@ -711,8 +771,8 @@ void axis_tables(int n, double a_tilde, int reach, int mmax, std::vector<double>
 // Eq. 66 in discrete form: along each axis the projection of chi must leave a
 // circular run of at least `reach` empty node indices, so no two nodes of Omega
 // are within the support through the periodic boundary.
-bool gap_ok(const std::vector<uint8_t>& chi, const int n[3], int reach) {
-  for (int ax = 0; ax < 3; ++ax) {
+bool gap_ok(const std::vector<uint8_t>& chi, const int n[3], int reach, int dim) {
+  for (int ax = 0; ax < dim; ++ax) {
     std::vector<uint8_t> occ(n[ax], 0);
     for (int k = 0; k < n[2]; ++k)
       for (int j = 0; j < n[1]; ++j)
@@ -857,6 +917,7 @@ cpx<float>*& spec_of<float>(rk_handle* h) { return h->spec32; }
 // the 1/(n_x n_y n_z) of the unnormalised transforms.
 rk_status ensure_precond(rk_handle* h) {
   if (h->pc_ready) return RK_OK;
+  if (h->dim < 3) return fail(RK_ERR_UNSUPPORTED, "spectral preconditioner: three-dimensional boxes only");
   if (h->parent) {
     // a clone shares the parent's symbol (set up once, on the first use by either)
     rk_handle* par = const_cast<rk_handle*>(h->parent);
@@ -867,7 +928,7 @@ rk_status ensure_precond(rk_handle* h) {
     for (int k = 0; k < 3; ++k)
       if (h->n[k] > 256) return fail(RK_ERR_UNSUPPORTED, "spectral preconditioner: box side above 256");
     int alpha[10][3];
-    basis_exponents(h->degree, alpha);
+    basis_exponents(h->degree, h->dim, alpha);
     std::vector<double> c[3];
     for (int ax = 0; ax < 3; ++ax) {
       const int n = h->n[ax];
@@ -1663,6 +1724,7 @@ rk_status scale_regular_rows(rk_handle* h, cudaStream_t s) {
   const int S = h->s, mmax = 2 * h->degree;
   h->zrows = mmax + 1;
   h->diag_reg = false;
+  if (h->dim < 3) return RK_OK;  // the fast path lives in the z pass
   if (!(h->breg64[3 * S] > 0.0)) return RK_OK;  // no regular node
   for (int k = 0; k < 3; ++k) {
     const double dk = h->breg64[k * S + 1 + k];
@@ -1883,9 +1945,12 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
   if (!grid || !chi || !V) return fail(RK_ERR_INVALID_ARG, "grid, chi and V are required");
   if (degree != 1 && degree != 2) return fail(RK_ERR_INVALID_ARG, "degree must be 1 or 2");
   if (!(a_tilde > 0.5 && a_tilde < 16.0)) return fail(RK_ERR_INVALID_ARG, "a_tilde out of range");
+  const int dim = grid->n[2] == 1 ? 2 : 3;  // a box one node thick in z is two-dimensional
+  if (grid->n[1] == 1) return fail(RK_ERR_UNSUPPORTED, "one-dimensional grids are not built");
   for (int k = 0; k < 3; ++k) {
-    if (grid->n[k] < 2 || !(grid->h[k] > 0.0)) return fail(RK_ERR_INVALID_ARG, "bad grid");
-    if (!supported_length(grid->n[k]))
+    if ((k < dim && grid->n[k] < 2) || grid->n[k] < 1 || !(grid->h[k] > 0.0))
+      return fail(RK_ERR_INVALID_ARG, "bad grid");
+    if (k < dim && !supported_length(grid->n[k]))
       return fail(RK_ERR_UNSUPPORTED, "box side " + std::to_string(grid->n[k]) + " not built");
   }
   if (grid->n[0] % 2 != 0 || ((long long)grid->n[1] * grid->n[2]) % 2 != 0)
@@ -1902,14 +1967,18 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
   }
   h->a_tilde = a_tilde;
   h->degree = degree;
-  h->s = degree == 1 ? 4 : 10;
+  h->dim = dim;
   h->nbox = (long long)grid->n[0] * grid->n[1] * grid->n[2];
   cudaGetDevice(&h->device);
-  h->chain.build(degree);
+  h->chain.build(degree, dim);
+  h->s = h->chain.s;
+  if (dim == 2)
+    for (int p = 0; p < h->s; ++p)
+      if (field_2d(h->chain, p) < 0) return bail(fail(RK_ERR_INVALID_ARG, "2D basis without a y-pass field"));
   int reach = 0;
   while (kernel_profile((double)(reach + 1) / a_tilde) > 0.0) ++reach;
   h->reach = reach;
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < dim; ++k)
     if (2 * reach + 1 > h->n[k]) return bail(fail(RK_ERR_UNSUPPORTED, "support wider than the box"));
   const long long n = h->nbox;
 
@@ -1935,7 +2004,7 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
     nom += hchi[i];
   }
   h->n_omega = nom;
-  if (!gap_ok(hchi, h->n, reach))
+  if (!gap_ok(hchi, h->n, reach, dim))
     return bail(fail(RK_ERR_UNSUPPORTED, "gap between the domain and its periodic image is narrower than the support (Eq. 66)"));
   e = cudaMemcpy(h->chi, hchi.data(), n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->chi_gamma, hgam.data(), n, cudaMemcpyHostToDevice);
@@ -1944,7 +2013,7 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
 
   // per-axis tables for m in [0, 2 deg] (moments need 2 deg; the chains use <= deg)
   const int mmax = 2 * degree;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < dim; ++k) {
     std::vector<double> coef;
     std::vector<cpx<double>> tw;
     axis_tables(h->n[k], a_tilde, reach, mmax, coef, tw);
@@ -1970,7 +2039,8 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
   std::vector<int> zbegin;
   for (auto& yg : ylist) {
     zbegin.push_back((int)zlist.size());
-    for (int gz = 0; yg.first + yg.second + gz <= D2; ++gz) zlist.push_back({yg.first, yg.second, gz});
+    for (int gz = 0; yg.first + yg.second + gz <= (dim == 3 ? D2 : yg.first + yg.second); ++gz)
+      zlist.push_back({yg.first, yg.second, gz});
   }
   const int nXm = D2 + 1, nYm = (int)ylist.size(), nZm = (int)zlist.size();
   double* mws = nullptr;
@@ -2023,13 +2093,15 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
       }
     }
     az.g_begin[nYm] = q;
-    RK_TRY(run_split<double>(h, 2, az, s));
+    // in 2D the y outputs are the moment fields (zlist = ylist with g_z = 0)
+    if (dim == 3) RK_TRY(run_split<double>(h, 2, az, s));
     // per-node M^{-1} -> b (Eq. 83-85)
     MomentArgs ma;
     memset(&ma, 0, sizeof(ma));
-    ma.mom = mf(1 + nXm + nYm);
+    ma.mom = dim == 3 ? mf(1 + nXm + nYm) : mf(1 + nXm);
     ma.n_mom = nZm;
     ma.s = h->s;
+    ma.dim = dim;
     const Chain& c = h->chain;
     for (int p = 0; p < h->s; ++p)
       for (int qq = 0; qq < h->s; ++qq) {

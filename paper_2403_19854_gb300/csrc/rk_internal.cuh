@@ -40,6 +40,7 @@ struct MomentArgs {
   const double* mom;            // moment fields [n_mom][nbox]
   int n_mom;
   int s;
+  int dim;                      // 3, or 2 (no z axis: b^z = 0)
   signed char pq[kMaxS][kMaxS]; // moment field of M_pq
   const uint8_t* chi;
   double inv_a[3];              // 1 / a_k
@@ -86,6 +87,15 @@ cudaError_t launch_gather(double* out, const double* src, long long stride, long
 // (cidx > 0), or g = 0 off chi (cidx = -1).
 template <typename T>
 cudaError_t launch_pointwise_stiff(const PointwiseArgs<T>& a, cudaStream_t s);
+// Alg. 3 without a z axis (2D): u = mask o sum_p b^0_p o D_p over the s fields D[p]
+template <typename T>
+cudaError_t launch_eval_u_fields(T* u, T* const* D, const T* b0, int s, const uint8_t* mask, long long n,
+                                 cudaStream_t st);
+// Alg. 4 without a z axis (2D): D[p] = w o b^0_p o y with w = wfield (or 1) times
+// wmask (or 1)
+template <typename T>
+cudaError_t launch_transpose_u_fields(T* const* D, const T* y, const T* b0, int s, const T* wfield,
+                                      const uint8_t* wmask, long long n, cudaStream_t st);
 // the pointwise stage on the listed 4-node groups only (after a z SPLIT with diag)
 template <typename T>
 cudaError_t launch_pointwise_groups(const PointwiseArgs<T>& a, const int* list, long long count, cudaStream_t s);

@@ -8,8 +8,9 @@ namespace rk {
 
 // ---------------------------------------------------------------- Alg. 1 tail
 // One thread per node: assemble M(x) from the moment fields (Eq. 48/80; M = I off
-// chi), Cholesky factorisation in FP64, rows 1..4 of M^{-1} by two triangular
-// solves, then b^0 = row 1, b^k = -(1/a_k) row (1+k) (Eq. 83-85, scaled basis).
+// chi), Cholesky factorisation in FP64, rows 1..1+dim of M^{-1} by two triangular
+// solves, then b^0 = row 1, b^k = -(1/a_k) row (1+k) (Eq. 83-85, scaled basis;
+// b^z = 0 in 2D).
 // A pivot <= 1e-14 * trace(M) marks the node singular: its b are set to 0 and the
 // node is counted.
 __global__ void __launch_bounds__(128) k_moment_solve(const MomentArgs a) {
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(128) k_moment_solve(const MomentArgs a) {
     for (int row = 0; row < 4; ++row) {
       double x[kMaxS];
       for (int p = 0; p < s; ++p) x[p] = (p == row) ? 1.0 : 0.0;
-      if (!bad) {
+      if (!bad && row <= a.dim) {  // b^k = 0 on an absent axis
         for (int p = 0; p < s; ++p) {
           double v = x[p];
           for (int k = 0; k < p; ++k) v -= L[p * (p + 1) / 2 + k] * x[k];

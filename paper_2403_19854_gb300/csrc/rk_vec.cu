@@ -246,6 +246,12 @@ cudaError_t launch_gather(double* out, const double* src, long long stride, long
   return cudaGetLastError();
 }
 
+// up to 10 field pointers by value (kernel arguments)
+template <typename T>
+struct DPtrs {
+  T* p[10];
+};
+
 // --------------------------------------------- pointwise stage of Alg. 2
 // Each thread owns VEC consecutive nodes (one 16-byte vector per field).
 template <typename T, int S>
@@ -306,12 +312,67 @@ cudaError_t launch_pointwise_stiff(const PointwiseArgs<T>& a, cudaStream_t s) {
   const long long nb = (a.nbox / VEC + 255) / 256;
   const unsigned grid = (unsigned)(nb < 152 * 16 ? (nb > 0 ? nb : 1) : 152 * 16);
   count_launch();
-  if (a.s == 4)
-    k_pointwise_stiff<T, 4><<<grid, 256, 0, s>>>(a);
-  else
-    k_pointwise_stiff<T, 10><<<grid, 256, 0, s>>>(a);
+  switch (a.s) {  // 3D bases (4, 10 monomials) and 2D bases (3, 6)
+    case 4: k_pointwise_stiff<T, 4><<<grid, 256, 0, s>>>(a); break;
+    case 10: k_pointwise_stiff<T, 10><<<grid, 256, 0, s>>>(a); break;
+    case 3: k_pointwise_stiff<T, 3><<<grid, 256, 0, s>>>(a); break;
+    case 6: k_pointwise_stiff<T, 6><<<grid, 256, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
+
+// ---------------------------------------- Alg. 3 / Alg. 4 without a z axis (2D)
+template <typename T>
+__global__ void k_eval_u_fields(T* u, DPtrs<T> D, const T* b0, int s, const uint8_t* mask, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    T acc = (T)0;
+    for (int p = 0; p < s; ++p) acc += b0[(long long)p * n + i] * D.p[p][i];
+    u[i] = (mask && !mask[i]) ? (T)0 : acc;
+  }
+}
+template <typename T>
+cudaError_t launch_eval_u_fields(T* u, T* const* D, const T* b0, int s, const uint8_t* mask, long long n,
+                                 cudaStream_t st) {
+  if (s < 1 || s > 10) return cudaErrorInvalidValue;
+  DPtrs<T> d;
+  for (int p = 0; p < s; ++p) d.p[p] = D[p];
+  const long long nb = (n + 255) / 256;
+  count_launch();
+  k_eval_u_fields<T><<<(unsigned)(nb < 152 * 16 ? (nb > 0 ? nb : 1) : 152 * 16), 256, 0, st>>>(u, d, b0, s, mask, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_eval_u_fields<float>(float*, float* const*, const float*, int, const uint8_t*, long long,
+                                                 cudaStream_t);
+template cudaError_t launch_eval_u_fields<double>(double*, double* const*, const double*, int, const uint8_t*,
+                                                  long long, cudaStream_t);
+
+template <typename T>
+__global__ void k_transpose_u_fields(DPtrs<T> D, const T* y, const T* b0, int s, const T* wfield,
+                                     const uint8_t* wmask, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    T w = y[i];
+    if (wfield) w *= wfield[i];
+    if (wmask && !wmask[i]) w = (T)0;
+    for (int p = 0; p < s; ++p) D.p[p][i] = b0[(long long)p * n + i] * w;
+  }
+}
+template <typename T>
+cudaError_t launch_transpose_u_fields(T* const* D, const T* y, const T* b0, int s, const T* wfield,
+                                      const uint8_t* wmask, long long n, cudaStream_t st) {
+  if (s < 1 || s > 10) return cudaErrorInvalidValue;
+  DPtrs<T> d;
+  for (int p = 0; p < s; ++p) d.p[p] = D[p];
+  const long long nb = (n + 255) / 256;
+  count_launch();
+  k_transpose_u_fields<T><<<(unsigned)(nb < 152 * 16 ? (nb > 0 ? nb : 1) : 152 * 16), 256, 0, st>>>(d, y, b0, s,
+                                                                                                    wfield, wmask, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_transpose_u_fields<float>(float* const*, const float*, const float*, int, const float*,
+                                                      const uint8_t*, long long, cudaStream_t);
+template cudaError_t launch_transpose_u_fields<double>(double* const*, const double*, const double*, int,
+                                                       const double*, const uint8_t*, long long, cudaStream_t);
 template cudaError_t launch_pointwise_stiff<float>(const PointwiseArgs<float>&, cudaStream_t);
 template cudaError_t launch_pointwise_stiff<double>(const PointwiseArgs<double>&, cudaStream_t);
 

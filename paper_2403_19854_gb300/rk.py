@@ -195,7 +195,7 @@ class Handle:
         self.n = tuple(int(v) for v in n)
         self.nbox = self.n[0] * self.n[1] * self.n[2]
         self.degree = int(degree)
-        self.s = 4 if degree == 1 else 10
+        self.s = (4 if degree == 1 else 10) if self.n[2] > 1 else (3 if degree == 1 else 6)  # 3D / 2D basis
         pc, kc = _ptr(chi)
         pg, kg = _ptr(chi_gamma)
         pV, kV = _ptr(V)
