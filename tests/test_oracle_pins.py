@@ -505,3 +505,44 @@ def test_manufactured_solution_quadratic_rate_1d_2d(dim):
         hs.append(p.h[0])
     rates = np.diff(np.log(errs)) / np.diff(np.log(hs))
     assert np.all(rates > 1.9) and np.all(rates < 2.1)
+
+
+def test_interior_shape_functions_closed_form_2d_a2():
+    """2D at a = 2h: the interior moment matrix is diag(1, 1/12, 1/12) (scaled basis),
+    so Psi_I(x_S) = w(o_x) w(o_y) and Psi^{grad x}_I(x_S) = o_x/(2h) w(o_y) with the
+    B-spline weights w = (1/6, 2/3, 1/6); the z gradient is 0 (no z axis)."""
+    p = W.plane_problem(16, 2.0, 1)
+    o = Oracle(p.n, p.h, 2.0, 1, p.chi)
+    nbr, psi, dpsi = o.shape_tables()
+    nb = o.node_box()
+    h = p.h[0]
+    w = _w_a2()
+    c = 6 + 16 * 7
+    S = int(np.searchsorted(nb, c))
+    assert o.nslot == 9
+    for sl in range(9):
+        ox, oy = sl % 3 - 1, sl // 3 - 1
+        assert psi[S, sl] == pytest.approx(float(w[ox] * w[oy]), abs=1e-15)
+        assert dpsi[S, sl, 0] * 2 * h == pytest.approx(float(ox * w[oy]), abs=1e-14)
+        assert dpsi[S, sl, 1] * 2 * h == pytest.approx(float(oy * w[ox]), abs=1e-14)
+        assert dpsi[S, sl, 2] == 0.0
+    bf = o.b_fields()
+    assert bf[0, :, c] == pytest.approx([1, 0, 0], abs=1e-14)
+    assert bf[1, :, c] * h == pytest.approx([0, -6, 0], abs=1e-12)   # -(1/a) * 12, a = 2h
+    assert np.all(bf[3] == 0.0)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_line_plane_inputs_trapezoidal_measure(dim):
+    """The nodal volumes of the line and plane problems are the trapezoidal rule on
+    [-1, 1]^dim: they sum to 2^dim and integrate the exact solution (a polynomial of
+    degree 2 per axis) with error O(h^2); the Dirichlet nodes are the boundary."""
+    p = W.line_problem(33, 1.5) if dim == 1 else W.plane_problem(33, 1.5)
+    assert p.V.sum() == pytest.approx(2.0 ** dim, rel=1e-14)
+    exact = 4.0 / 3.0 if dim == 1 else (4.0 / 3.0) ** 2
+    assert abs((p.V * p.u_exact).sum() - exact) < 2 * p.h[0] ** 2
+    X, Y, _ = p.coords()
+    X, Y = X - 1.0, Y - 1.0
+    on = p.chi > 0
+    bnd = (np.isclose(np.abs(X), 1.0) | ((dim == 2) & np.isclose(np.abs(Y), 1.0))) & on
+    assert np.array_equal(p.chi_gamma > 0, bnd)
