@@ -64,3 +64,26 @@ def test_invalid_arguments_rejected_without_gpu(libpath):
     g.n[0] = 17
     assert L.rk_setup(ctypes.byref(g), dummy, None, dummy, 1, 2.0, None, ctypes.byref(out)) == 8
     assert not out.value
+
+
+def test_grid_dimension_checks_without_gpu(libpath):
+    """A box one node thick in z is two-dimensional; one node thick in y (1D) is not
+    built (RK_ERR_UNSUPPORTED) and a first axis of one node is invalid -- all decided
+    before any device work."""
+    import ctypes
+
+    from paper_2403_19854_gb300 import rk
+    L = rk.lib()
+    out = ctypes.c_void_p()
+    dummy = (ctypes.c_uint8 * 8)()
+    g = rk.Grid()
+    for k in range(3):
+        g.h[k] = 0.1
+    g.n[0], g.n[1], g.n[2] = 32, 1, 1
+    assert L.rk_setup(ctypes.byref(g), dummy, None, dummy, 1, 1.5, None, ctypes.byref(out)) == 8
+    assert b"one-dimensional" in L.rk_last_error_message()
+    g.n[0], g.n[1], g.n[2] = 1, 32, 32
+    assert L.rk_setup(ctypes.byref(g), dummy, None, dummy, 1, 1.5, None, ctypes.byref(out)) == 1
+    g.n[0], g.n[1], g.n[2] = 32, 20, 1       # 2D, but a y side that is not built
+    assert L.rk_setup(ctypes.byref(g), dummy, None, dummy, 1, 1.5, None, ctypes.byref(out)) == 8
+    assert not out.value
