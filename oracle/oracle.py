@@ -69,6 +69,8 @@ def _load():
     for name in ("orc_s", "orc_dim"):
         getattr(lib, name).restype = ctypes.c_int
         getattr(lib, name).argtypes = [ctypes.c_void_p]
+    lib.orc_eval_points_1d.restype = ctypes.c_int64
+    lib.orc_eval_points_1d.argtypes = [ctypes.c_void_p, ctypes.c_int64, _f64p, _f64p, _f64p]
     lib.orc_grid_dim.restype = ctypes.c_int
     lib.orc_grid_dim.argtypes = [_intp]
     lib.orc_basis_size_dim.restype = ctypes.c_int
@@ -209,6 +211,19 @@ class Oracle:
         d, pd = _f64(np.asarray(d).reshape(-1))
         u = np.zeros(self.nbox)
         _load().orc_eval_u(self._h, pd, u.ctypes.data_as(_f64p))
+        return u
+
+    def eval_points_1d(self, x, d) -> np.ndarray:
+        """u^h(x) = sum_I Psi_I(x) d_I at arbitrary points of a 1D grid (Eq. 1-2); x is
+        measured from grid node 0."""
+        x, px = _f64(np.asarray(x).reshape(-1))
+        d, pd = _f64(np.asarray(d).reshape(-1))
+        u = np.zeros(x.size)
+        bad = _load().orc_eval_points_1d(self._h, x.size, px, pd, u.ctypes.data_as(_f64p))
+        if bad < 0:
+            raise ValueError("oracle: eval_points_1d needs a 1D grid")
+        if bad > 0:
+            raise ArithmeticError(f"oracle: {bad} points with a singular moment matrix")
         return u
 
     def eval_u_transpose(self, e) -> np.ndarray:

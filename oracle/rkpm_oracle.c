@@ -490,6 +490,53 @@ void orc_eval_u(const orc_ctx *c, const double *d, double *u) {
   }
 }
 
+/*
+ * Eq. 1-2 at arbitrary points of a 1D grid: u^h(x) = sum_I Psi_I(x) d_I with
+ * Psi_I(x) = b(x)^T H((x - x_I)/a) phi(|x - x_I|/a) and M(x) of Eq. 3 summed over
+ * the chi nodes I within the support (x measured from grid node 0, node i at i h).
+ * Used for the Gauss-quadrature L2 error of Eq. 100.  Returns the number of points
+ * whose M(x) was singular (their value is 0), or -1 if the grid is not 1D.
+ */
+int64_t orc_eval_points_1d(const orc_ctx *c, int64_t npts, const double *x, const double *d, double *u) {
+  const geom_t *g = &c->g;
+  if (g->dim != 1) return -1;
+  const int s = g->s;
+  const double h = g->h[0], a = g->a[0];
+  int64_t bad = 0;
+  for (int64_t q = 0; q < npts; ++q) {
+    u[q] = 0.0;
+    const int i0 = (int)floor(x[q] / h);
+    double M[ORC_MAXS * ORC_MAXS], H[ORC_MAXS];
+    memset(M, 0, sizeof(M));
+    for (int i = i0 - g->r[0] - 1; i <= i0 + g->r[0] + 1; ++i) {
+      if (i < 0 || i >= g->n[0] || !g->chi[i]) continue;
+      const double xi[3] = {(x[q] - i * h) / a, 0.0, 0.0};
+      const double ph = orc_phi1(fabs(xi[0]));
+      if (ph == 0.0) continue;
+      basis(g->degree, 1, xi, H);
+      for (int p = 0; p < s; ++p)
+        for (int r = 0; r < s; ++r) M[p * s + r] += H[p] * H[r] * ph;
+    }
+    if (cholesky(s, M)) { ++bad; continue; }
+    double b0[ORC_MAXS];
+    for (int p = 0; p < s; ++p) b0[p] = p == 0 ? 1.0 : 0.0;
+    chol_solve(s, M, b0); /* first row of M^{-1} (Eq. 45) */
+    double v = 0.0;
+    for (int i = i0 - g->r[0] - 1; i <= i0 + g->r[0] + 1; ++i) {
+      if (i < 0 || i >= g->n[0] || !g->chi[i]) continue;
+      const double xi[3] = {(x[q] - i * h) / a, 0.0, 0.0};
+      const double ph = orc_phi1(fabs(xi[0]));
+      if (ph == 0.0) continue;
+      basis(g->degree, 1, xi, H);
+      double psi = 0.0;
+      for (int p = 0; p < s; ++p) psi += b0[p] * H[p];
+      v += psi * ph * d[i];
+    }
+    u[q] = v;
+  }
+  return bad;
+}
+
 /* Transpose of Eq. 62: w_J = sum_I Psi_J(x_I) e_I. */
 void orc_eval_u_transpose(const orc_ctx *c, const double *e, double *w) {
   const int ns = c->g.nslot;

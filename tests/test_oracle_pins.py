@@ -546,3 +546,44 @@ def test_line_plane_inputs_trapezoidal_measure(dim):
     on = p.chi > 0
     bnd = (np.isclose(np.abs(X), 1.0) | ((dim == 2) & np.isclose(np.abs(Y), 1.0))) & on
     assert np.array_equal(p.chi_gamma > 0, bnd)
+
+
+def test_arbitrary_point_evaluation_1d_reproduces_and_matches_nodes():
+    """Eq. 1-2 at arbitrary points: the linear basis reproduces any linear field
+    exactly everywhere (d_I = alpha + beta x_I gives u^h(x) = alpha + beta x), and at
+    the nodes the value equals Eq. 62 (the nodal evaluation)."""
+    p = W.line_problem(40, 2.5, 1)
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    h = p.h[0]
+    n_om = p.meta["n_omega_side"]
+    rng = np.random.default_rng(7)
+    x = rng.uniform(0.0, (n_om - 1) * h, 200)
+    X = np.arange(p.nbox) * h
+    d = np.where(p.chi > 0, 0.3 - 1.7 * X, 0.0)
+    assert np.abs(o.eval_points_1d(x, d) - (0.3 - 1.7 * x)).max() < 1e-12
+    d2 = W.random_field(p.nbox, 3)
+    nodes = np.arange(n_om) * h
+    assert np.abs(o.eval_points_1d(nodes, d2) - o.eval_u(d2 * p.chi)[:n_om]).max() < 1e-13
+
+
+def test_paper_1d_gauss_quadrature_error_rate():
+    """Sec. 6.1.1 measures the L2 error of Eq. 100 with 5 Gauss points per cell; the
+    paper reports the quadratic rate (Fig. 9).  a = 1.5h, linear basis, N = 2^4 ... 2^8."""
+    gx, gw = np.polynomial.legendre.leggauss(5)
+    errs, hs = [], []
+    for nb in (16, 32, 64, 128, 256):
+        p = W.line_problem(nb, 1.5, 1)
+        o = Oracle(p.n, p.h, 1.5, 1, p.chi)
+        d, info = o.solve(p.V, p.chi_gamma, p.r, p.g, tol=1e-13)
+        assert info["converged"]
+        h = p.h[0]
+        n_om = p.meta["n_omega_side"]
+        left = np.arange(n_om - 1) * h
+        xq = (left[:, None] + 0.5 * h * (gx[None, :] + 1.0)).reshape(-1)
+        wq = np.tile(0.5 * h * gw, n_om - 1)
+        uh = o.eval_points_1d(xq, d)
+        ue = 1.0 - (xq - 1.0) ** 2           # node 0 sits at x = -1
+        errs.append(np.sqrt((wq * (uh - ue) ** 2).sum()))
+        hs.append(h)
+    rates = np.diff(np.log(errs)) / np.diff(np.log(hs))
+    assert np.all(rates > 1.9) and np.all(rates < 2.1), rates
