@@ -591,18 +591,11 @@ rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uin
     }
   }
   az.g_begin[c.nY] = q;
-  PointwiseArgs<T> pw;
-  memset(&pw, 0, sizeof(pw));
+  PointwiseArgs<T> pw = pointwise_base<T>(h);
   for (int p = 0; p < h->s; ++p) pw.D[p] = h->ws<T>(dbase + p);
-  pw.s = h->s;
-  pw.cidx = h->cidx;
-  pw.ctab = ctab_of<T>(h);
-  pw.n_irr = h->n_irr;
-  for (int j = 0; j < 3 * h->s + 1; ++j) pw.breg[j] = breg_of<T>(h, j);
-  pw.nbox = h->nbox;
   if (h->n[0] % 4 == 0 && h->diag_reg) {
     // with diagonal interior coefficients the z SPLIT writes g_x, g_y, g_z of the
-    // regular nodes directly (scaled multiplier rows) and zeroes the rest of the
+    // regular nodes directly (scaled multiplier rows) and 0 for the other g_p of the
     // regular and outside groups; the boundary groups follow in a short kernel
     for (int qq = 0; qq < q; ++qq)
       for (int k = 0; k < 3; ++k)
