@@ -1283,6 +1283,8 @@ rk_status solve_masked(rk_handle* h, const double* F, double* x, const rk_solve_
   double fn;
   RK_TRY(norm2(h, F, &fn, s));
   info->f_norm = fn;
+  if (!std::isfinite(fn))
+    return fail(RK_ERR_INVALID_ARG, "right-hand side is not finite (NaN or Inf in r, g or the Neumann data)");
   if (fn == 0.0) {
     RK_CK(launch_fill<double>(x, 0.0, n, s));
     info->rel_residual = 0.0;
@@ -1316,7 +1318,7 @@ rk_status solve_masked(rk_handle* h, const double* F, double* x, const rk_solve_
   }
   info->iterations = total;
   info->rel_residual = rn / fn;
-  if (rn > target) return fail(RK_ERR_NOT_CONVERGED, "tolerance not reached");
+  if (!(rn <= target)) return fail(RK_ERR_NOT_CONVERGED, "tolerance not reached");  // also a NaN residual
   return RK_OK;
 }
 
@@ -1515,7 +1517,7 @@ rk_status transient_implicit(rk_handle* h, const double* f, const double* g, dou
     double tr;
     RK_TRY(dot(t, t, &tr));
     info->rel_residual = std::max(info->rel_residual, std::sqrt(tr) / bn);
-    if (std::sqrt(tr) > 10.0 * o.tol * bn) return fail(RK_ERR_NOT_CONVERGED, "implicit step not converged");
+    if (!(std::sqrt(tr) <= 10.0 * o.tol * bn)) return fail(RK_ERR_NOT_CONVERGED, "implicit step not converged");
   }
   RK_CK(launch_add(d, x, dG, n, s));
   return RK_OK;
@@ -1633,7 +1635,7 @@ rk_status solve_nonlinear(rk_handle* h, const double* r, const double* g, int ki
   info->iterations = it;
   info->rel_residual = rr0 > 0.0 ? std::sqrt(rr / rr0) : 0.0;
   RK_CK(launch_add(d, x, dG, n, s));
-  if (std::sqrt(rr) > target) return fail(RK_ERR_NOT_CONVERGED, "nonlinear CG: tolerance not reached");
+  if (!(std::sqrt(rr) <= target)) return fail(RK_ERR_NOT_CONVERGED, "nonlinear CG: tolerance not reached");
   return RK_OK;
 }
 
@@ -1843,6 +1845,8 @@ rk_status prepare_mixed_job(rk_handle* h, const double* r, const double* g, cons
   double fn;
   RK_TRY(norm2(h, F, &fn, s));
   info->f_norm = fn;
+  if (!std::isfinite(fn))
+    return fail(RK_ERR_INVALID_ARG, "right-hand side is not finite (NaN or Inf in r or g)");
   j.h = h;
   j.s = s;
   j.o = o;
@@ -2256,7 +2260,7 @@ rk_status rk_solve_batched(const rk_batch_item* items, int32_t n_items, const rk
     MixedJob& j = jobs[i];
     inf[i].iterations = j.it;
     inf[i].rel_residual = j.fn > 0.0 ? j.rn / j.fn : 0.0;
-    if (inf[i].status == RK_OK && j.rn > j.target) inf[i].status = RK_ERR_NOT_CONVERGED;
+    if (inf[i].status == RK_OK && !(j.rn <= j.target)) inf[i].status = RK_ERR_NOT_CONVERGED;
     RK_CK(launch_add((double*)sd[i].dev, h->v64(5), h->v64(0), h->nbox, h->bstream));
     if (su[i].dev) RK_TRY(op_U<double>(h, (const double*)sd[i].dev, (double*)su[i].dev, h->bstream));
     RK_TRY(stage_out_finish(sd[i], h->bstream));
