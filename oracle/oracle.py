@@ -40,11 +40,16 @@ _intp = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library with gcc (plain C, no arch flags)."""
+    """Compile the oracle shared library with gcc (plain C, no arch flags; OpenMP
+    when available, which threads the loops over nodes, rows and samples)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        try:  # all host threads where the compiler has OpenMP; serial otherwise
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -54,6 +59,8 @@ def _load():
     if _lib is not None:
         return _lib
     lib = ctypes.CDLL(build())
+    lib.orc_threads.restype = ctypes.c_int
+    lib.orc_threads.argtypes = []
     lib.orc_phi1.restype = ctypes.c_double
     lib.orc_phi1.argtypes = [ctypes.c_double]
     lib.orc_create.restype = ctypes.c_void_p
@@ -116,6 +123,11 @@ def _u8(a):
 def _i64(a):
     a = np.ascontiguousarray(a, dtype=np.int64)
     return a, a.ctypes.data_as(_i64p)
+
+
+def threads() -> int:
+    """Host threads the oracle's loops run on (1 without OpenMP)."""
+    return int(_load().orc_threads())
 
 
 def phi1(z: float) -> float:

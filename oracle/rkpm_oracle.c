@@ -39,8 +39,24 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXS 10
+
+/* Threads.  Loops over nodes, rows or samples whose iterations are independent
+   run on all host threads (OpenMP, when the library is built with it); every
+   value is computed by one thread in the same order whatever the thread count,
+   and sums across nodes (dot products) add fixed blocks in block order, so the
+   results do not depend on the number of threads. */
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Kernel and basis                                                          */
@@ -333,17 +349,24 @@ orc_ctx *orc_create(const int n[3], const double h[3], double a_tilde, int degre
     if (c->box_node[i] >= 0) c->node_box[c->box_node[i]] = i;
   c->nsingular = 0;
   c->first_singular = -1;
+  uint8_t *bad = (uint8_t *)calloc((size_t)c->nnode + 1, 1);
+  if (!bad) { orc_destroy(c); return NULL; }
+#pragma omp parallel for schedule(dynamic, 256)
   for (int64_t S = 0; S < c->nnode; ++S) {
-    int bad = shape_at(&c->g, c->node_box[S], c->psi + S * c->g.nslot,
-                       c->dpsi + S * c->g.nslot * 3, c->b + S * 4 * c->g.s);
-    if (bad) {
-      if (c->first_singular < 0) c->first_singular = c->node_box[S];
-      c->nsingular++;
+    bad[S] = (uint8_t)shape_at(&c->g, c->node_box[S], c->psi + S * c->g.nslot,
+                               c->dpsi + S * c->g.nslot * 3, c->b + S * 4 * c->g.s);
+    if (bad[S]) {
       memset(c->psi + S * c->g.nslot, 0, sizeof(double) * c->g.nslot);
       memset(c->dpsi + S * c->g.nslot * 3, 0, sizeof(double) * c->g.nslot * 3);
       memset(c->b + S * 4 * c->g.s, 0, sizeof(double) * 4 * c->g.s);
     }
   }
+  for (int64_t S = 0; S < c->nnode; ++S)
+    if (bad[S]) {
+      if (c->first_singular < 0) c->first_singular = c->node_box[S];
+      c->nsingular++;
+    }
+  free(bad);
   return c;
 }
 
@@ -434,11 +457,33 @@ static int64_t nbr_node(const orc_ctx *c, int64_t S, int sl) {
   return c->box_node[gidx(g, cI[0], cI[1], cI[2])];
 }
 
-/* Eq. 50 with direct nodal integration (Eq. 54), matrix-free:
-   g^k_S = sum_J Psi^{grad k}_J(x_S) d_J;  f_I = sum_S V_S sum_k Psi^{grad k}_I(x_S) g^k_S. */
+/* Evaluation node S = I + sigma whose support holds node I (I sits in slot
+   -sigma of S), for the slot of offset sigma; -1 if there is none. */
+static int64_t covering_node(const orc_ctx *c, int64_t I, int sl, int *slot_of_I) {
+  const geom_t *g = &c->g;
+  int cI[3], sig[3];
+  gcoord(g, c->node_box[I], cI);
+  offset_of(g, sl, sig);
+  int cS[3] = {cI[0] + sig[0], cI[1] + sig[1], cI[2] + sig[2]};
+  if (cS[0] < 0 || cS[0] >= g->n[0] || cS[1] < 0 || cS[1] >= g->n[1] || cS[2] < 0 || cS[2] >= g->n[2])
+    return -1;
+  int msig[3] = {-sig[0], -sig[1], -sig[2]};
+  *slot_of_I = slot_of(g, msig);
+  return c->box_node[gidx(g, cS[0], cS[1], cS[2])];
+}
+
+/* Eq. 50 with direct nodal integration (Eq. 54), matrix-free, both sums written
+   as gathers: g^k_S = sum_J Psi^{grad k}_J(x_S) d_J at every evaluation node S,
+   then f_I = sum_S V_S sum_k Psi^{grad k}_I(x_S) g^k_S over the S whose support
+   holds I. */
 void orc_apply_K(const orc_ctx *c, const double *V, const double *d, double *f) {
   const int ns = c->g.nslot;
-  for (int64_t i = 0; i < c->nbox; ++i) f[i] = 0.0;
+  double *G = (double *)malloc(sizeof(double) * (size_t)(3 * c->nnode + 1));
+  if (!G) {
+    for (int64_t i = 0; i < c->nbox; ++i) f[i] = NAN;
+    return;
+  }
+#pragma omp parallel for schedule(static)
   for (int64_t S = 0; S < c->nnode; ++S) {
     double gk[3] = {0.0, 0.0, 0.0};
     const double *dp = c->dpsi + S * ns * 3;
@@ -450,34 +495,52 @@ void orc_apply_K(const orc_ctx *c, const double *V, const double *d, double *f) 
       gk[1] += dp[3 * sl + 1] * dJ;
       gk[2] += dp[3 * sl + 2] * dJ;
     }
-    double VS = V[c->node_box[S]];
-    for (int sl = 0; sl < ns; ++sl) {
-      int64_t I = nbr_node(c, S, sl);
-      if (I < 0) continue;
-      f[c->node_box[I]] += VS * (dp[3 * sl + 0] * gk[0] + dp[3 * sl + 1] * gk[1] + dp[3 * sl + 2] * gk[2]);
-    }
+    G[3 * S + 0] = gk[0];
+    G[3 * S + 1] = gk[1];
+    G[3 * S + 2] = gk[2];
   }
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < c->nbox; ++i) f[i] = 0.0;
+#pragma omp parallel for schedule(static)
+  for (int64_t I = 0; I < c->nnode; ++I) {
+    double acc = 0.0;
+    for (int sl = 0; sl < ns; ++sl) {
+      int tI;
+      int64_t S = covering_node(c, I, sl, &tI);
+      if (S < 0) continue;
+      const double *dI = c->dpsi + (S * ns + tI) * 3;
+      acc += V[c->node_box[S]] * (dI[0] * G[3 * S + 0] + dI[1] * G[3 * S + 1] + dI[2] * G[3 * S + 2]);
+    }
+    f[c->node_box[I]] = acc;
+  }
+  free(G);
 }
 
-/* Eq. 27 with direct nodal integration (Eq. 59): f^r_I = sum_S V_S Psi_I(x_S) r_S. */
+/* Eq. 27 with direct nodal integration (Eq. 59): f^r_I = sum_S V_S Psi_I(x_S) r_S,
+   gathered over the S whose support holds I. */
 void orc_rhs(const orc_ctx *c, const double *V, const double *r, double *fr) {
   const int ns = c->g.nslot;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < c->nbox; ++i) fr[i] = 0.0;
-  for (int64_t S = 0; S < c->nnode; ++S) {
-    double w = V[c->node_box[S]] * r[c->node_box[S]];
-    const double *ps = c->psi + S * ns;
+#pragma omp parallel for schedule(static)
+  for (int64_t I = 0; I < c->nnode; ++I) {
+    double acc = 0.0;
     for (int sl = 0; sl < ns; ++sl) {
-      int64_t I = nbr_node(c, S, sl);
-      if (I < 0) continue;
-      fr[c->node_box[I]] += ps[sl] * w;
+      int tI;
+      int64_t S = covering_node(c, I, sl, &tI);
+      if (S < 0) continue;
+      acc += c->psi[S * ns + tI] * (V[c->node_box[S]] * r[c->node_box[S]]);
     }
+    fr[c->node_box[I]] = acc;
   }
 }
 
 /* Eq. 62: u^h(x_I) = sum_J Psi_J(x_I) d_J at every node. */
 void orc_eval_u(const orc_ctx *c, const double *d, double *u) {
   const int ns = c->g.nslot;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < c->nbox; ++i) u[i] = 0.0;
+#pragma omp parallel for schedule(static)
   for (int64_t S = 0; S < c->nnode; ++S) {
     const double *ps = c->psi + S * ns;
     double v = 0.0;
@@ -537,18 +600,22 @@ int64_t orc_eval_points_1d(const orc_ctx *c, int64_t npts, const double *x, cons
   return bad;
 }
 
-/* Transpose of Eq. 62: w_J = sum_I Psi_J(x_I) e_I. */
+/* Transpose of Eq. 62: w_J = sum_I Psi_J(x_I) e_I, gathered over the nodes I
+   whose support holds J. */
 void orc_eval_u_transpose(const orc_ctx *c, const double *e, double *w) {
   const int ns = c->g.nslot;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < c->nbox; ++i) w[i] = 0.0;
-  for (int64_t S = 0; S < c->nnode; ++S) {
-    const double *ps = c->psi + S * ns;
-    double eS = e[c->node_box[S]];
+#pragma omp parallel for schedule(static)
+  for (int64_t J = 0; J < c->nnode; ++J) {
+    double acc = 0.0;
     for (int sl = 0; sl < ns; ++sl) {
-      int64_t J = nbr_node(c, S, sl);
-      if (J < 0) continue;
-      w[c->node_box[J]] += ps[sl] * eS;
+      int tJ;
+      int64_t I = covering_node(c, J, sl, &tJ);
+      if (I < 0) continue;
+      acc += c->psi[I * ns + tJ] * e[c->node_box[I]];
     }
+    w[c->node_box[J]] = acc;
   }
 }
 
@@ -556,83 +623,141 @@ void orc_eval_u_transpose(const orc_ctx *c, const double *e, double *w) {
 /* Assembled stiffness matrix (Eq. 26 with DNI), CSR over node numbers       */
 /* ------------------------------------------------------------------------ */
 
-/* Returns the number of nonzeros, or -1 on allocation failure. */
-int64_t orc_assemble_K(orc_ctx *c, const double *V) {
+/* Row I of K (Eq. 26 with DNI): K_IJ = sum_S V_S sum_k Psi^{grad k}_I(x_S)
+   Psi^{grad k}_J(x_S) over the quadrature nodes S whose support holds I, each
+   pair (I, J) accumulated in a local window of offsets J - I; the nonzeros are
+   appended to (*col, *val) in window order.  Returns 0, or -1 on allocation
+   failure. */
+typedef struct {
+  int64_t n, cap;
+  int64_t *col;
+  double *val;
+} orc_rowbuf;
+
+static int assemble_row(const orc_ctx *c, const double *V, int64_t I, double *acc, uint8_t *hit, orc_rowbuf *rb) {
   const geom_t *g = &c->g;
   const int ns = g->nslot;
-  int W[3] = {4 * g->r[0] + 1, 4 * g->r[1] + 1, 4 * g->r[2] + 1};
-  int64_t nloc = (int64_t)W[0] * W[1] * W[2];
-  double *acc = (double *)calloc((size_t)nloc, sizeof(double));
-  uint8_t *hit = (uint8_t *)calloc((size_t)nloc, 1);
+  const int W[3] = {4 * g->r[0] + 1, 4 * g->r[1] + 1, 4 * g->r[2] + 1};
+  const int64_t nloc = (int64_t)W[0] * W[1] * W[2];
+  int cI[3];
+  gcoord(g, c->node_box[I], cI);
+  /* quadrature nodes S whose support covers I: S = I + sigma, and I sits in
+     slot (-sigma) of S */
+  for (int sl = 0; sl < ns; ++sl) {
+    int sig[3];
+    offset_of(g, sl, sig);
+    int cS[3] = {cI[0] + sig[0], cI[1] + sig[1], cI[2] + sig[2]};
+    if (cS[0] < 0 || cS[0] >= g->n[0] || cS[1] < 0 || cS[1] >= g->n[1] || cS[2] < 0 || cS[2] >= g->n[2])
+      continue;
+    int64_t S = c->box_node[gidx(g, cS[0], cS[1], cS[2])];
+    if (S < 0) continue;
+    int msig[3] = {-sig[0], -sig[1], -sig[2]};
+    const double *dI = c->dpsi + (S * ns + slot_of(g, msig)) * 3;
+    if (dI[0] == 0.0 && dI[1] == 0.0 && dI[2] == 0.0) continue;
+    double VS = V[c->node_box[S]];
+    for (int tl = 0; tl < ns; ++tl) {
+      int64_t J = nbr_node(c, S, tl);
+      if (J < 0) continue;
+      int tau[3];
+      offset_of(g, tl, tau);
+      const double *dJ = c->dpsi + (S * ns + tl) * 3;
+      int64_t li = ((int64_t)(sig[2] + tau[2] + 2 * g->r[2]) * W[1] + (sig[1] + tau[1] + 2 * g->r[1])) * W[0] +
+                   (sig[0] + tau[0] + 2 * g->r[0]);
+      acc[li] += VS * (dI[0] * dJ[0] + dI[1] * dJ[1] + dI[2] * dJ[2]);
+      hit[li] = 1;
+    }
+  }
+  for (int64_t li = 0; li < nloc; ++li) {
+    if (!hit[li]) continue;
+    int o[3] = {(int)(li % W[0]) - 2 * g->r[0], (int)((li / W[0]) % W[1]) - 2 * g->r[1],
+                (int)(li / ((int64_t)W[0] * W[1])) - 2 * g->r[2]};
+    int cJ[3] = {cI[0] + o[0], cI[1] + o[1], cI[2] + o[2]};
+    int64_t J = c->box_node[gidx(g, cJ[0], cJ[1], cJ[2])];
+    if (rb->n >= rb->cap) {
+      int64_t ncap = rb->cap * 2 + 1024;
+      int64_t *nc = (int64_t *)realloc(rb->col, sizeof(int64_t) * (size_t)ncap);
+      if (nc) rb->col = nc;
+      double *nv = (double *)realloc(rb->val, sizeof(double) * (size_t)ncap);
+      if (nv) rb->val = nv;
+      if (!nc || !nv) return -1;
+      rb->cap = ncap;
+    }
+    rb->col[rb->n] = J;
+    rb->val[rb->n] = acc[li];
+    ++rb->n;
+    acc[li] = 0.0;
+    hit[li] = 0;
+  }
+  return 0;
+}
+
+/* Assemble K as CSR over node numbers: contiguous blocks of rows per thread,
+   concatenated in row order.  Returns the number of nonzeros, or -1 on
+   allocation failure. */
+int64_t orc_assemble_K(orc_ctx *c, const double *V) {
+  const geom_t *g = &c->g;
+  const int64_t nloc = (int64_t)(4 * g->r[0] + 1) * (4 * g->r[1] + 1) * (4 * g->r[2] + 1);
   free(c->kptr);
   free(c->kcol);
   free(c->kval);
+  c->kcol = NULL;
+  c->kval = NULL;
   c->kptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(c->nnode + 1));
-  int64_t cap = c->nnode * (int64_t)(nloc < 4096 ? nloc : 4096) + 1;
-  c->kcol = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
-  c->kval = (double *)malloc(sizeof(double) * (size_t)cap);
-  if (!acc || !hit || !c->kptr || !c->kcol || !c->kval) {
+  if (!c->kptr) return -1;
+  const int nt = orc_threads();
+  orc_rowbuf *rb = (orc_rowbuf *)calloc((size_t)nt, sizeof(orc_rowbuf));
+  if (!rb) return -1;
+  int failed = 0;
+#pragma omp parallel num_threads(nt)
+  {
+#ifdef _OPENMP
+    const int t = omp_get_thread_num(), nth = omp_get_num_threads();
+#else
+    const int t = 0, nth = 1;
+#endif
+    const int64_t lo = c->nnode * t / nth, hi = c->nnode * (t + 1) / nth;
+    double *acc = (double *)calloc((size_t)nloc, sizeof(double));
+    uint8_t *hit = (uint8_t *)calloc((size_t)nloc, 1);
+    if (!acc || !hit) {
+#pragma omp atomic write
+      failed = 1;
+    } else {
+      for (int64_t I = lo; I < hi; ++I) {
+        if (assemble_row(c, V, I, acc, hit, &rb[t])) {
+#pragma omp atomic write
+          failed = 1;
+          break;
+        }
+        c->kptr[I + 1] = rb[t].n;  /* row end within this thread's block, offset below */
+      }
+    }
     free(acc);
     free(hit);
-    return -1;
   }
   int64_t nnz = 0;
-  c->kptr[0] = 0;
-  for (int64_t I = 0; I < c->nnode; ++I) {
-    int cI[3];
-    gcoord(g, c->node_box[I], cI);
-    /* quadrature nodes S whose support covers I: S = I + sigma, and I sits in
-       slot (-sigma) of S */
-    for (int sl = 0; sl < ns; ++sl) {
-      int sig[3];
-      offset_of(g, sl, sig);
-      int cS[3] = {cI[0] + sig[0], cI[1] + sig[1], cI[2] + sig[2]};
-      if (cS[0] < 0 || cS[0] >= g->n[0] || cS[1] < 0 || cS[1] >= g->n[1] || cS[2] < 0 || cS[2] >= g->n[2])
-        continue;
-      int64_t S = c->box_node[gidx(g, cS[0], cS[1], cS[2])];
-      if (S < 0) continue;
-      int msig[3] = {-sig[0], -sig[1], -sig[2]};
-      const double *dI = c->dpsi + (S * ns + slot_of(g, msig)) * 3;
-      if (dI[0] == 0.0 && dI[1] == 0.0 && dI[2] == 0.0) continue;
-      double VS = V[c->node_box[S]];
-      for (int tl = 0; tl < ns; ++tl) {
-        int64_t J = nbr_node(c, S, tl);
-        if (J < 0) continue;
-        int tau[3];
-        offset_of(g, tl, tau);
-        const double *dJ = c->dpsi + (S * ns + tl) * 3;
-        int64_t li = ((int64_t)(sig[2] + tau[2] + 2 * g->r[2]) * W[1] + (sig[1] + tau[1] + 2 * g->r[1])) * W[0] +
-                     (sig[0] + tau[0] + 2 * g->r[0]);
-        acc[li] += VS * (dI[0] * dJ[0] + dI[1] * dJ[1] + dI[2] * dJ[2]);
-        hit[li] = 1;
-      }
-    }
-    for (int64_t li = 0; li < nloc; ++li) {
-      if (!hit[li]) continue;
-      int o[3] = {(int)(li % W[0]) - 2 * g->r[0], (int)((li / W[0]) % W[1]) - 2 * g->r[1],
-                  (int)(li / ((int64_t)W[0] * W[1])) - 2 * g->r[2]};
-      int cJ[3] = {cI[0] + o[0], cI[1] + o[1], cI[2] + o[2]};
-      int64_t J = c->box_node[gidx(g, cJ[0], cJ[1], cJ[2])];
-      if (nnz >= cap) {
-        int64_t ncap = cap * 2;
-        int64_t *nc = (int64_t *)realloc(c->kcol, sizeof(int64_t) * (size_t)ncap);
-        double *nv = (double *)realloc(c->kval, sizeof(double) * (size_t)ncap);
-        if (!nc || !nv) { free(acc); free(hit); return -1; }
-        c->kcol = nc;
-        c->kval = nv;
-        cap = ncap;
-      }
-      c->kcol[nnz] = J;
-      c->kval[nnz] = acc[li];
-      ++nnz;
-      acc[li] = 0.0;
-      hit[li] = 0;
-    }
-    c->kptr[I + 1] = nnz;
+  if (!failed) {
+    for (int t = 0; t < nt; ++t) nnz += rb[t].n;
+    c->kcol = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz + 1));
+    c->kval = (double *)malloc(sizeof(double) * (size_t)(nnz + 1));
+    if (!c->kcol || !c->kval) failed = 1;
   }
-  free(acc);
-  free(hit);
-  return nnz;
+  if (!failed) {
+    int64_t off = 0;
+    c->kptr[0] = 0;
+    for (int t = 0; t < nt; ++t) {
+      const int64_t lo = c->nnode * t / nt, hi = c->nnode * (t + 1) / nt;
+      for (int64_t I = lo; I < hi; ++I) c->kptr[I + 1] += off;
+      memcpy(c->kcol + off, rb[t].col, sizeof(int64_t) * (size_t)rb[t].n);
+      memcpy(c->kval + off, rb[t].val, sizeof(double) * (size_t)rb[t].n);
+      off += rb[t].n;
+    }
+  }
+  for (int t = 0; t < nt; ++t) {
+    free(rb[t].col);
+    free(rb[t].val);
+  }
+  free(rb);
+  return failed ? -1 : nnz;
 }
 
 void orc_get_K(const orc_ctx *c, int64_t *ptr, int64_t *col, double *val) {
@@ -647,6 +772,7 @@ void orc_get_K(const orc_ctx *c, int64_t *ptr, int64_t *col, double *val) {
 
 /* y = K_OO x over free nodes (free[I] = 1), x and y indexed by node number */
 static void spmv_free(const orc_ctx *c, const uint8_t *freem, const double *x, double *y) {
+#pragma omp parallel for schedule(static)
   for (int64_t I = 0; I < c->nnode; ++I) {
     if (!freem[I]) { y[I] = 0.0; continue; }
     double v = 0.0;
@@ -656,9 +782,23 @@ static void spmv_free(const orc_ctx *c, const uint8_t *freem, const double *x, d
   }
 }
 
+/* a . b as the ordered sum of the partial sums of fixed blocks of 4096 entries */
+#define ORC_DOT_BLOCK 4096
 static double dotn(int64_t n, const double *a, const double *b) {
+  const int64_t nb = (n + ORC_DOT_BLOCK - 1) / ORC_DOT_BLOCK;
+  double stackp[64];
+  double *part = nb <= 64 ? stackp : (double *)malloc(sizeof(double) * (size_t)nb);
+  if (!part) return NAN;
+#pragma omp parallel for schedule(static)
+  for (int64_t blk = 0; blk < nb; ++blk) {
+    const int64_t lo = blk * ORC_DOT_BLOCK, hi = lo + ORC_DOT_BLOCK < n ? lo + ORC_DOT_BLOCK : n;
+    double s = 0.0;
+    for (int64_t i = lo; i < hi; ++i) s += a[i] * b[i];
+    part[blk] = s;
+  }
   double s = 0.0;
-  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  for (int64_t blk = 0; blk < nb; ++blk) s += part[blk];
+  if (part != stackp) free(part);
   return s;
 }
 
@@ -759,14 +899,17 @@ int orc_solve_dirichlet(const orc_ctx *c, const uint8_t *chi_gamma, const double
       double pap = dotn(nn, p, t);
       if (!(pap > 0.0)) { ret = -2; break; }
       double alpha = rr / pap;
+#pragma omp parallel for schedule(static)
       for (int64_t I = 0; I < nn; ++I) { xf[I] += alpha * p[I]; r[I] -= alpha * t[I]; }
       double rr2 = dotn(nn, r, r);
       double beta = rr2 / rr;
       rr = rr2;
+#pragma omp parallel for schedule(static)
       for (int64_t I = 0; I < nn; ++I) p[I] = r[I] + beta * p[I];
       ++it;
       if (it % 50 == 0) { /* replace the recurrence by the true residual */
         spmv_free(c, freem, xf, t);
+#pragma omp parallel for schedule(static)
         for (int64_t I = 0; I < nn; ++I) r[I] = freem[I] ? b[I] - t[I] : 0.0;
         rr = dotn(nn, r, r);
       }
@@ -792,7 +935,9 @@ done:
 
 /* y = K x for grid-indexed x (all chi nodes), from the assembled CSR */
 void orc_spmv(const orc_ctx *c, const double *x, double *y) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < c->nbox; ++i) y[i] = 0.0;
+#pragma omp parallel for schedule(static)
   for (int64_t I = 0; I < c->nnode; ++I) {
     double v = 0.0;
     for (int64_t e = c->kptr[I]; e < c->kptr[I + 1]; ++e) v += c->kval[e] * x[c->node_box[c->kcol[e]]];
@@ -815,14 +960,21 @@ int64_t orc_apply_K_sampled(const int n[3], const double h[3], double a_tilde, i
                             int64_t nsample, const int64_t *sample, double *out) {
   geom_t g;
   if (geom_init(&g, n, h, a_tilde, degree, chi)) return -1;
+  int64_t bad = 0;
+  int failed = 0;
+#pragma omp parallel reduction(+ : bad)
+  {
   double *psi = (double *)malloc(sizeof(double) * (size_t)g.nslot);
   double *dpsi = (double *)malloc(sizeof(double) * (size_t)g.nslot * 3);
-  if (!psi || !dpsi) { free(psi); free(dpsi); return -1; }
-  int64_t bad = 0;
+  if (!psi || !dpsi) {
+#pragma omp atomic write
+    failed = 1;
+  }
+#pragma omp for schedule(dynamic, 1)
   for (int64_t q = 0; q < nsample; ++q) {
     int64_t I = sample[q];
     out[q] = 0.0;
-    if (!chi[I]) continue;
+    if (!chi[I] || !psi || !dpsi) continue;
     int cI[3];
     gcoord(&g, I, cI);
     double acc = 0.0;
@@ -855,7 +1007,8 @@ int64_t orc_apply_K_sampled(const int n[3], const double h[3], double a_tilde, i
   }
   free(psi);
   free(dpsi);
-  return bad;
+  }
+  return failed ? -1 : bad;
 }
 
 /*
@@ -867,12 +1020,20 @@ int64_t orc_b_sampled(const int n[3], const double h[3], double a_tilde, int deg
                       const uint8_t *chi, int64_t nsample, const int64_t *sample, double *out) {
   geom_t g;
   if (geom_init(&g, n, h, a_tilde, degree, chi)) return -1;
+  int64_t bad = 0;
+  int failed = 0;
+#pragma omp parallel reduction(+ : bad)
+  {
   double *psi = (double *)malloc(sizeof(double) * (size_t)g.nslot);
   double *dpsi = (double *)malloc(sizeof(double) * (size_t)g.nslot * 3);
-  if (!psi || !dpsi) { free(psi); free(dpsi); return -1; }
-  int64_t bad = 0;
+  if (!psi || !dpsi) {
+#pragma omp atomic write
+    failed = 1;
+  }
+#pragma omp for schedule(dynamic, 1)
   for (int64_t q = 0; q < nsample; ++q) {
     double *o = out + q * 4 * g.s;
+    if (!psi || !dpsi) continue;
     if (!chi[sample[q]]) {
       for (int i = 0; i < 4 * g.s; ++i) o[i] = 0.0;
       o[0] = 1.0;
@@ -883,5 +1044,6 @@ int64_t orc_b_sampled(const int n[3], const double h[3], double a_tilde, int deg
   }
   free(psi);
   free(dpsi);
-  return bad;
+  }
+  return failed ? -1 : bad;
 }
