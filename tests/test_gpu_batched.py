@@ -187,21 +187,29 @@ def test_batched_item_matches_oracle(batch):
 
 
 def test_stalled_mixed_solve_finishes_in_fp64():
-    """A quadratic (a = 3h) cube: the mixed iterations stall on the near-zero-energy
-    modes (kappa ~ 3e7 at 16^3) and the FP64 finish takes over from the current iterate; its FP64 residual
-    must end below what the mixed iterations alone reached."""
-    p = W.cube_problem(16, 3.0, 2, "sin")
+    """The hand-over of a mixed solve to FP64 CG (Alg. 5 with iterative refinement:
+    when the FP32 iterations stop reducing the FP64 residual, or the refinement-step
+    cap is reached, the solve continues with FP64 CG from the current iterate).
+    The cap of two refinement steps forces the hand-over on any device: after two
+    residual replacements (each at a tenth of the previous FP64 residual) the
+    residual is near 1e-2, far above tol.  The finished solve must reach tol with
+    FP64 iterations, and its d must match the oracle's direct solve of the assembled
+    Dirichlet system (Eq. 29) to 1e-9; with fp64_finish = 0 the same cap ends the
+    solve unconverged at the residual of the mixed iterations."""
+    p = W.cube_problem(32, 2.5, 1, "sin")
+    p.g = np.where(p.chi_gamma > 0, 0.1 * W.random_field(p.nbox, 5), 0.0)
     H = rk.Handle.from_problem(p, device=DEV)
     r, g = tdev(p.r), tdev(p.g)
-    _, _, i0 = H.solve(r, g, precision="mixed", tol=1e-10, fp64_finish=0, max_iter=20000, raise_on_error=False)
-    _, _, i1 = H.solve(r, g, precision="mixed", tol=1e-10, fp64_finish=1, max_iter=20000, raise_on_error=False)
-    _, _, i2 = H.solve(r, g, precision="fp64", tol=1e-10, max_iter=20000, raise_on_error=False)
-    assert i0["fp64_iterations"] == 0
-    if i0["status"] == 0:
-        pytest.skip("mixed iterations converged on this device")
-    assert i1["fp64_iterations"] > 0
-    assert i1["rel_residual"] < i0["rel_residual"]
-    assert i1["rel_residual"] <= max(1e-10, 10 * i2["rel_residual"])
+    _, _, i0 = H.solve(r, g, precision="mixed", tol=1e-13, fp64_finish=0, max_outer=2, raise_on_error=False)
+    d1, u1, i1 = H.solve(r, g, precision="mixed", tol=1e-13, fp64_finish=1, max_outer=2, raise_on_error=False)
+    assert i0["status"] == 5 and i0["fp64_iterations"] == 0 and i0["outer"] == 2
+    assert i0["rel_residual"] > 1e-6
+    assert i1["status"] == 0 and i1["fp64_iterations"] > 0
+    assert i1["rel_residual"] <= 1e-13 < i0["rel_residual"]
+    o = Oracle(p.n, p.h, p.a_tilde, p.degree, p.chi)
+    do, _ = o.solve(p.V, p.chi_gamma, p.r, p.g, tol=1e-13)  # CG on the assembled CSR
+    assert rel(np_(d1), do) < 1e-9
+    assert rel(np_(u1), o.eval_u(do)) < 1e-9
     H.close()
 
 

@@ -5,9 +5,15 @@ Tolerances (relative L2 over the domain nodes, 0 required off the domain):
                        rounding: Sec. 6.1, "identical up to the machine precision")
   FP32 path   2e-6    (single-precision FFT convolutions: a few ulps of FP32,
                        ~6e-8, times the O(log N) growth of the transforms and the
-                       two chained convolutions of Alg. 2; measured 2-5e-7)
+                       two chained convolutions of Alg. 2; measured 2-5e-7 at
+                       16^3-32^3 and 4.6e-7 / 9.4e-7 (L2 / max) at 256^3, where
+                       log2 N is twice that of 16^3)
   mixed solve 1e-9 against the FP64 solution after FP64 refinement.
+Each comparison checks the relative L2 error and the max-norm error relative to
+the largest reference value, both against the same tolerance.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -33,6 +39,22 @@ def rel(a, b, m=None):
     if m is not None:
         a, b = a[m], b[m]
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def relmax(a, b, m=None):
+    """Max-norm error relative to the largest reference value: one wrong node among
+    many cannot hide under a small relative L2 error."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if m is not None:
+        a, b = a[m], b[m]
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def close(a, b, tol, m=None, what=""):
+    """Relative L2 and relative max-norm error both within tol."""
+    e2, ei = rel(a, b, m), relmax(a, b, m)
+    assert e2 < tol and ei < tol, f"{what}: rel L2 {e2:.3e}, rel max {ei:.3e} (tol {tol:.0e})"
 
 
 def tdev(x, dtype=None):
@@ -74,7 +96,7 @@ def test_setup_coefficients_alg1(case):
     bg = np_(H.get_b(torch.empty(4 * p.s * p.nbox, dtype=torch.float64, device=DEV)))
     bo = o.b_fields()
     for i in range(4):
-        assert rel(bg[i][:, m], bo[i][:, m]) < TOL64, f"b family {i}"
+        close(bg[i][:, m], bo[i][:, m], TOL64, what=f"b family {i}")
     assert H.singular == (0, -1)
 
 
@@ -84,7 +106,7 @@ def test_stiffness_action_fp64_alg2(case):
     d = W.random_field(p.nbox, 3)
     f = np_(H.apply_K(tdev(d)))
     fo = o.apply_K(p.V, d * p.chi)
-    assert rel(f, fo, m) < TOL64
+    close(f, fo, TOL64, m)
     assert np.all(f[~m] == 0.0)
 
 
@@ -94,7 +116,7 @@ def test_stiffness_action_fp32_alg2(case):
     d = W.random_field(p.nbox, 4).astype(np.float32)
     f = np_(H.apply_K(tdev(d))).astype(np.float64)
     fo = o.apply_K(p.V, d.astype(np.float64) * p.chi)
-    assert rel(f, fo, m) < TOL32
+    close(f, fo, TOL32, m)
     assert np.all(f[~m] == 0.0)
 
 
@@ -103,7 +125,7 @@ def test_rhs_alg4(case):
     m = p.chi > 0
     r = W.random_field(p.nbox, 5)
     fr = np_(H.rhs(tdev(r)))
-    assert rel(fr, o.rhs(p.V, r * p.chi), m) < TOL64
+    close(fr, o.rhs(p.V, r * p.chi), TOL64, m)
     assert np.all(fr[~m] == 0.0)
 
 
@@ -112,9 +134,9 @@ def test_eval_u_alg3_and_transpose(case):
     m = p.chi > 0
     d = W.random_field(p.nbox, 6)
     u = np_(H.eval_u(tdev(d)))
-    assert rel(u, o.eval_u(d * p.chi), m) < TOL64
+    close(u, o.eval_u(d * p.chi), TOL64, m)
     w = np_(H.eval_u_transpose(tdev(d)))
-    assert rel(w, o.eval_u_transpose(d * p.chi), m) < TOL64
+    close(w, o.eval_u_transpose(d * p.chi), TOL64, m)
     assert np.all(u[~m] == 0.0) and np.all(w[~m] == 0.0)
 
 
@@ -140,24 +162,35 @@ def test_solve_alg5_matches_oracle(nb, a, prec):
     uo = o.eval_u(do)
     d, u, info = H.solve(tdev(p.r), tdev(p.g), precision=prec, tol=1e-13)
     assert info["rel_residual"] <= 1e-13
-    assert rel(np_(d), do) < 1e-9
-    assert rel(np_(u), uo) < 1e-9
+    close(np_(d), do, 1e-9)
+    close(np_(u), uo, 1e-9)
     gam = p.chi_gamma > 0
     assert np.array_equal(np_(d)[gam], p.g[gam])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_adjoint_matches_oracle_gradient(prec):
-    """dJ/dr and dJ/dg from the adjoint solve against the oracle's assembled-K gradient."""
-    p = W.adjoint_problem(n_box=16, a_tilde=2.5, degree=1, sigma=0.2)
-    H = rk.Handle.from_problem(p, device=DEV)
+@functools.lru_cache(maxsize=None)
+def _oracle_adjoint(nb):
+    """The oracle's gradient: direct solves at 16^3; at 32^3 CG on the assembled
+    CSR to 1e-13 (the adjoint system does not reach 1e-14 in FP64 CG there)."""
+    p = W.adjoint_problem(n_box=nb, a_tilde=2.5, degree=1, sigma=0.2)
     o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    Jo, gro, ggo, _, _ = o.adjoint(p.V, p.chi, p.chi_gamma, p.r, p.g, p.meta["u_target"],
+                                   tol=1e-14 if nb <= 16 else 1e-13)
+    return p, Jo, gro, ggo
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nb", [16, 32])
+def test_adjoint_matches_oracle_gradient(prec, nb):
+    """dJ/dr and dJ/dg from the adjoint solve against the oracle's assembled-K
+    gradient."""
+    p, Jo, gro, ggo = _oracle_adjoint(nb)
+    H = rk.Handle.from_problem(p, device=DEV)
     ut = p.meta["u_target"]
-    Jo, gro, ggo, _, _ = o.adjoint(p.V, p.chi, p.chi_gamma, p.r, p.g, ut)
     J, gr, gg, info = H.solve_adjoint(tdev(p.r), tdev(p.g), tdev(ut), precision=prec, tol=1e-13)
     assert abs(J - Jo) <= 1e-10 * Jo
-    assert rel(np_(gr), gro) < 1e-8
-    assert rel(np_(gg), ggo) < 1e-8
+    close(np_(gr), gro, 1e-8)
+    close(np_(gg), ggo, 1e-8)
 
 
 @pytest.mark.parametrize("nb,a,deg", [(128, 2.5, 1), (96, 2.5, 1), (64, 3.0, 2)])
@@ -175,13 +208,69 @@ def test_full_size_sampled_parity(nb, a, deg):
     f64 = np_(H.apply_K(tdev(d)))
     f32 = np_(H.apply_K(tdev(d.astype(np.float32)))).astype(np.float64)
     fo = apply_K_sampled(p.n, p.h, a, deg, p.chi, p.V, d, sample)
-    assert rel(f64[sample], fo) < TOL64
+    close(f64[sample], fo, TOL64)
     fo32 = apply_K_sampled(p.n, p.h, a, deg, p.chi, p.V, d.astype(np.float32).astype(np.float64), sample)
-    assert rel(f32[sample], fo32) < 10 * TOL32
+    close(f32[sample], fo32, TOL32)
     bg = np_(H.get_b(torch.empty(4 * p.s * p.nbox, dtype=torch.float64, device=DEV)))
     bo = b_sampled(p.n, p.h, a, deg, p.chi, sample)
     for i in range(4):
-        assert rel(bg[i][:, sample].T, bo[:, i, :]) < TOL64
+        close(bg[i][:, sample].T, bo[:, i, :], TOL64)
+
+
+def cube_sample(nb, a, n_random=24, seed=0):
+    """Grid indices of a structured sample of the cube's domain nodes: the 8 corners,
+    nodes on the 12 edges, on the 6 faces, on every layer from the face inwards to
+    the first regular layer (the first whose support lies in the domain) on each
+    axis, and random interior nodes."""
+    n_om = nb - int(np.floor(a))
+    reach = int(np.ceil(a)) - 1
+    L = n_om - 1
+    rng = np.random.default_rng(seed)
+    pts = [(i, j, k) for i in (0, L) for j in (0, L) for k in (0, L)]
+    for t in (1, L // 3, L - 1):
+        pts += [(t, 0, 0), (0, t, L), (L, L, t), (0, L, t), (t, L, 0), (L, t, L)]
+    for f in range(6):
+        ax, side = f // 2, (0 if f % 2 == 0 else L)
+        for _ in range(2):
+            c = list(rng.integers(1, L, 2))
+            c.insert(ax, side)
+            pts.append(tuple(c))
+    for layer in range(1, reach + 2):
+        for ax in range(3):
+            for side in (layer, L - layer):
+                c = list(rng.integers(reach + 1, L - reach, 2))
+                c.insert(ax, side)
+                pts.append(tuple(c))
+    pts += [tuple(rng.integers(0, n_om, 3)) for _ in range(n_random)]
+    return np.unique(np.array([i + nb * (j + nb * k) for i, j, k in pts], dtype=np.int64))
+
+
+def test_full_size_sampled_parity_cube256_linear():
+    """The benchmarked operator itself: the 256^3-box cube, a = 2.5h, linear basis,
+    whose z split writes g of the regular nodes through the scaled multiplier rows
+    and leaves the boundary groups to the pointwise kernel.  K.u in FP64 and FP32
+    and b at >= 64 structured sample nodes (corners, edges, faces, each layer up to
+    the first regular one, interior), each recomputed by the oracle from scratch
+    (Alg. 2 against the neighbour sums of Eq. 50/54)."""
+    nb, a = 256, 2.5
+    p = W.cube_problem(nb, a, 1, "sin")
+    H = rk.Handle.from_problem(p, device=DEV)
+    sample = cube_sample(nb, a, seed=256)
+    assert sample.size >= 64 and np.all(p.chi[sample] == 1)
+    d = W.random_field(p.nbox, 9)
+    f64 = np_(H.apply_K(tdev(d)))
+    fo = apply_K_sampled(p.n, p.h, a, 1, p.chi, p.V, d, sample)
+    close(f64[sample], fo, TOL64, what="FP64 K.u")
+    d32 = d.astype(np.float32)
+    f32 = np_(H.apply_K(tdev(d32))).astype(np.float64)
+    fo32 = apply_K_sampled(p.n, p.h, a, 1, p.chi, p.V, d32.astype(np.float64), sample)
+    close(f32[sample], fo32, TOL32, what="FP32 K.u")
+    assert np.all(f64[p.chi == 0] == 0.0) and np.all(f32[p.chi == 0] == 0.0)
+    bg = np_(H.get_b(torch.empty(4 * p.s * p.nbox, dtype=torch.float64, device=DEV)))
+    bo = b_sampled(p.n, p.h, a, 1, p.chi, sample)
+    for i in range(4):
+        close(bg[i][:, sample].T, bo[:, i, :], TOL64, what=f"b family {i}")
+    H.close()
 
 
 def test_full_size_sampled_parity_spheres256_quadratic():
@@ -197,14 +286,14 @@ def test_full_size_sampled_parity_spheres256_quadratic():
     d = W.random_field(p.nbox, 9) * p.chi
     f64 = np_(H.apply_K(tdev(d)))
     fo = apply_K_sampled(p.n, p.h, 3.0, 2, p.chi, p.V, d, sample)
-    assert rel(f64[sample], fo) < TOL64
+    close(f64[sample], fo, TOL64)
     f32 = np_(H.apply_K(tdev(d.astype(np.float32)))).astype(np.float64)
     fo32 = apply_K_sampled(p.n, p.h, 3.0, 2, p.chi, p.V, d.astype(np.float32).astype(np.float64), sample)
-    assert rel(f32[sample], fo32) < 10 * TOL32
+    close(f32[sample], fo32, TOL32)
     bg = np_(H.get_b(torch.empty(4 * p.s * p.nbox, dtype=torch.float64, device=DEV)))
     bo = b_sampled(p.n, p.h, 3.0, 2, p.chi, sample)
     for i in range(4):
-        assert rel(bg[i][:, sample].T, bo[:, i, :]) < TOL64
+        close(bg[i][:, sample].T, bo[:, i, :], TOL64)
     H.close()
 
 
@@ -247,24 +336,24 @@ def test_support_sweep_tab4_tab5(a, deg):
     bg = np_(H.get_b(torch.empty(4 * p.s * p.nbox, dtype=torch.float64, device=DEV)))
     bo = o.b_fields()
     for i in range(4):
-        assert rel(bg[i][:, m], bo[i][:, m]) < TOL64, f"b family {i}"
+        close(bg[i][:, m], bo[i][:, m], TOL64, what=f"b family {i}")
     d = W.random_field(p.nbox, 13)
     fo = o.apply_K(p.V, d * p.chi)
     f = np_(H.apply_K(tdev(d)))
-    assert rel(f, fo, m) < TOL64
+    close(f, fo, TOL64, m)
     assert np.all(f[~m] == 0.0)
     f32 = np_(H.apply_K(tdev(d.astype(np.float32)))).astype(np.float64)
-    assert rel(f32, o.apply_K(p.V, d.astype(np.float32).astype(np.float64) * p.chi), m) < TOL32
+    close(f32, o.apply_K(p.V, d.astype(np.float32).astype(np.float64) * p.chi), TOL32, m)
     H.close()
 
 
 def test_paper_3d_problem_converges_quadratically_on_the_gpu():
     """Sec. 6.1.3 (Eq. 106-108: a = 1.5h, linear basis, u = prod(1 - x_k^2) on
     [-1, 1]^3), solved on the GPU (mixed precision with FP64 refinement) at boxes
-    32^3, 64^3, 128^3: the nodal normalised L2 error of Eq. 104 falls at the quadratic
+    16^3 ... 256^3: the nodal normalised L2 error of Eq. 104 falls at the quadratic
     rate the paper states for n = 1 (the oracle gives 1.95-1.99 over 16^3-48^3)."""
     errs, hs = [], []
-    for nb in (32, 64, 128):
+    for nb in (16, 32, 64, 128, 256):
         p = W.cube_problem(nb, 1.5, 1, "paper", -1.0, 1.0)
         H = rk.Handle.from_problem(p, device=DEV)
         d, u, info = H.solve(tdev(p.r), tdev(p.g), precision="mixed", tol=1e-11)
