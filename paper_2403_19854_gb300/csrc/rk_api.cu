@@ -178,6 +178,7 @@ struct rk_handle {
   std::vector<CUtensorMap> tmaps32[2], tmaps64[2];
   int* err_host = nullptr;   // mapped pinned word: a bounded device wait gave up
   int* err_dev = nullptr;    // its device address
+  int short_wait = 0;        // rk_debug_short_waits: first waits for input tiles give up at once
   // spectral preconditioner: half spectra (per handle, rows of nxp complex); the
   // per-axis symbol factors, the symbol parameters and the multiplier tables live
   // in the set-up handle and are shared with its clones
@@ -337,6 +338,7 @@ PassArgs<T> pass_base(const rk_handle* h, int axis) {
   PassArgs<T> a;
   memset(&a, 0, sizeof(a));
   a.err = h->err_dev;
+  a.short_wait = h->short_wait;
   a.coef_rows = 2 * h->degree + 1;
   a.coef = coef_of<T>(h, axis);
   a.tw = tw_of<T>(h, axis);
@@ -1222,8 +1224,13 @@ rk_status mixed_check(MixedJob& j) {
   if (j.rn < 0.5 * j.best) {
     j.best = j.rn;
     j.stall = 0;
-  } else if (++j.stall >= kStallReplacements || j.info->outer >= j.o.max_outer) {
-    j.done = true;  // the FP32 recurrence no longer reduces the FP64 residual
+  } else {
+    ++j.stall;
+  }
+  // the FP32 recurrence no longer reduces the FP64 residual, or the cap on
+  // refinement steps is reached
+  if (j.stall >= kStallReplacements || j.info->outer >= j.o.max_outer) {
+    j.done = true;
     j.fp64_tail = true;
     return RK_OK;
   }
@@ -2318,6 +2325,17 @@ rk_status rk_apply_K(rk_handle* h, const void* d, void* f, int32_t dtype, void* 
     RK_CK(cudaStreamSynchronize(s));
     RK_TRY(check_device_flag(h));
   }
+  return RK_OK;
+}
+
+rk_status rk_debug_short_waits(rk_handle* h, int32_t enable) {
+  if (!h) return fail(RK_ERR_INVALID_ARG, "handle is NULL");
+  if (enable != 0 && enable != 1) return fail(RK_ERR_INVALID_ARG, "enable must be 0 or 1");
+  h->short_wait = enable;
+  // a captured chunk of CG iterations holds the pass arguments it was captured with
+  if (h->chunk_graph) cudaGraphExecDestroy(h->chunk_graph);
+  h->chunk_graph = nullptr;
+  h->chunk_len = 0;
   return RK_OK;
 }
 
