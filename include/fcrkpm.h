@@ -337,6 +337,22 @@ rk_status rk_profile_read(rk_handle* h, double* ms, int64_t* launches, int32_t n
 const char* rk_profile_class_name(int32_t cls);
 
 /*
+ * rk_debug_short_waits -- a diagnostic switch for tests of the time-out path (the
+ * paper has no counterpart).  While enable = 1, the first bounded wait of every
+ * block of this handle's TMA-fed passes for an input tile gives up at once: the
+ * block records the time-out in the handle's error word, still waits (with the
+ * normal limit) for its copy in flight to land, and returns without writing its
+ * outputs.  The next call of the handle that synchronises (a solve, or a call on
+ * host arrays) then returns RK_ERR_TIMEOUT and clears the word; results computed
+ * meanwhile are invalid.  enable = 0 restores the normal waits of 2^26 polls.
+ * Passes fed by cp.async copies (boxes whose rows are not a multiple of 16 bytes)
+ * have no bounded wait and are unaffected.  Drops the handle's captured CUDA
+ * graph of CG iterations (it holds the pass arguments it was captured with).
+ * Errors: RK_ERR_INVALID_ARG for a NULL handle or enable not 0 or 1.
+ */
+rk_status rk_debug_short_waits(rk_handle* h, int32_t enable);
+
+/*
  * rk_apply_K_noalloc -- f = K d (the FP64 result of rk_apply_K) without allocating
  * any memory.  The paper has no counterpart: this entry point exists for callers
  * that cannot allocate device memory -- code running inside a host application
@@ -344,22 +360,33 @@ const char* rk_profile_class_name(int32_t cls);
  * which a cudaMalloc/cudaFree (which may synchronise the device) is not allowed.
  * The caller passes every input and the output; the intermediate fields and the
  * per-axis tables live in one fixed device array of RK_NOALLOC_MAX_DOUBLES doubles
- * (about 16.8 MB) that every GPU loading this library holds until the process
- * exits.
+ * (about 16.8 MB), plus a few KB of flags and axis projections, that every GPU
+ * loading this library holds until the process exits.
  *   grid, degree, a_tilde  as for rk_setup (the same built box sides)
  *   chi   uint8[nbox]  device, Eq. 40 (input and output mask)
  *   chiV  double[nbox] device, chi o V
  *   b     double[4*s*nbox] device, the coefficients in the layout of rk_get_b
  *   d, f  double[nbox] device, input and output
+ * Every array must be device memory of the current device, aligned to 16 bytes
+ * (host arrays, which the other entry points stage, would need buffers): else
+ * RK_ERR_INVALID_ARG before any device work.
  * Limit: (n+1 + 2*n_Y) * nbox + 8192 <= RK_NOALLOC_MAX_DOUBLES with n_Y = 3 (degree
- * 1) or 6 (degree 2): up to a 64^3 box for degree 1, 32^3 for degree 2; larger
- * boxes return RK_ERR_UNSUPPORTED before any device work.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the one array and overwrite it (every
- * value is written before it is read within a call), so calls whose GPU work
- * overlaps -- on different streams or host threads -- race and must be ordered
- * by the caller.
+ * 1) or 6 (degree 2): up to a 64^3 box for degree 1 and a 48^3 box for degree 2
+ * (any built sides whose product fits); larger boxes return RK_ERR_UNSUPPORTED
+ * before any device work.
+ * Gap: like rk_setup, the call checks the Eq. 66 gap of chi (a circular run of
+ * empty node indices at least as long as the support's reach on every axis), on
+ * the device; it waits for that check (a synchronisation of `stream`) and returns
+ * RK_ERR_UNSUPPORTED, with f untouched, when chi is too close to its periodic
+ * image.  The rest of the work is queued on `stream` without waiting.
+ * Every call looks up the device addresses of the fixed arrays for the current
+ * device (cudaGetSymbolAddress, which allocates nothing); the first call on a
+ * device also loads the library's kernels there, so make it before any stream
+ * capture.  Should a bounded wait for an input tile give up inside the passes, f
+ * is filled with NaN.  All calls share the one array and overwrite it (every value
+ * is written before it is read within a call; the flags are cleared at the start
+ * of each call), so calls whose GPU work overlaps -- on different streams or host
+ * threads -- race and must be ordered by the caller.
  */
 #define RK_NOALLOC_MAX_DOUBLES 2105344LL
 rk_status rk_apply_K_noalloc(const rk_grid* grid, int32_t degree, double a_tilde, const uint8_t* chi,

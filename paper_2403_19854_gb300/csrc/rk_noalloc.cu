@@ -8,9 +8,10 @@
 // The caller passes the inputs and the output; the intermediate fields of the
 // five passes and the per-axis tables live in one file-scope device array of
 // fixed size (RK_NOALLOC_MAX_DOUBLES doubles, about 16.8 MB), which every GPU
-// that loads this library holds until the process exits.
+// that loads this library holds until the process exits, next to two small
+// arrays for the status flags and the axis projections of chi.
+#include <algorithm>
 #include <cstring>
-#include <mutex>
 
 #include "fcrkpm.h"
 #include "rk_internal.cuh"
@@ -20,29 +21,86 @@ namespace {
 
 constexpr long long kTableDoubles = 8192;  // per-axis multiplier rows and twiddles
 static_assert(RK_NOALLOC_MAX_DOUBLES > kTableDoubles, "scratch too small");
+constexpr int kMaxSide = 1024;             // box side covered by the projection array
 
 static __device__ __align__(256) double g_noalloc_scratch[RK_NOALLOC_MAX_DOUBLES];
+// [0]: a bounded wait for an input tile gave up; [1]: chi violates the gap of Eq. 66
+static __device__ __align__(16) int g_noalloc_flags[4];
+// occupied node indices of chi along x, y, z (n0 + n1 + n2 bytes)
+static __device__ __align__(16) uint8_t g_noalloc_proj[3 * kMaxSide];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_addr_mu;
-double* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array for the current device (the host-side name
-// is only a stand-in).  Looked up once per device, with that device current.
-cudaError_t scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+// Device address of a file-scope array for the current device: the host-side
+// name is only a stand-in.  Looked up on every call (no allocation), so it also
+// holds after a device reset or on another device.
+template <typename P, typename Sym>
+cudaError_t symbol_address(P** out, const Sym& sym) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, sym);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_addr[dev];
+  *out = static_cast<P*>(p);
   return cudaSuccess;
+}
+
+// An array the kernels may read or write in place: device (or managed) memory of
+// the current device, aligned to 16 bytes.
+bool device_array_ok(const void* p, int dev) {
+  if (!p || reinterpret_cast<uintptr_t>(p) % 16 != 0) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// proj[i] = 1 (x), proj[n0 + j] = 1 (y), proj[n0 + n1 + k] = 1 (z) for every node
+// (i, j, k) of chi; each block gathers its nodes in shared memory first.
+__global__ void k_noalloc_project(const uint8_t* chi, int n0, int n1, int n2, long long nbox, uint8_t* proj) {
+  __shared__ uint8_t loc[3 * kMaxSide];
+  const int np = n0 + n1 + n2;
+  for (int t = threadIdx.x; t < np; t += blockDim.x) loc[t] = 0;
+  __syncthreads();
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nbox;
+       idx += (long long)gridDim.x * blockDim.x) {
+    if (!chi[idx]) continue;
+    const long long jk = idx / n0;
+    loc[idx - jk * n0] = 1;
+    loc[n0 + (int)(jk % n1)] = 1;
+    loc[n0 + n1 + (int)(jk / n1)] = 1;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < np; t += blockDim.x)
+    if (loc[t]) proj[t] = 1;
+}
+
+// Eq. 66 in discrete form (as rk_setup checks it): along each axis the occupied
+// indices must leave a circular run of at least `reach` empty ones; flag = 1 if
+// not.  One thread per axis.
+__global__ void k_noalloc_gap(const uint8_t* proj, int n0, int n1, int n2, int reach, int* flag) {
+  const int ax = threadIdx.x;
+  if (ax >= 3) return;
+  const int n = ax == 0 ? n0 : (ax == 1 ? n1 : n2);
+  const uint8_t* occ = proj + (ax == 0 ? 0 : (ax == 1 ? n0 : n0 + n1));
+  int best = 0, run = 0;
+  bool any = false;
+  for (int t = 0; t < 2 * n; ++t) {
+    if (occ[t % n]) {
+      any = true;
+      run = 0;
+    } else {
+      run = min(run + 1, n);
+      best = max(best, run);
+    }
+  }
+  if (any && best < reach) *flag = 1;
+}
+
+// f = NaN when a pass recorded a wait that gave up
+__global__ void k_noalloc_poison(double* f, long long nbox, const int* flag) {
+  if (!*(volatile const int*)flag) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nbox; i += (long long)gridDim.x * blockDim.x)
+    f[i] = __longlong_as_double(0x7ff8000000000000LL);
 }
 
 __device__ double noalloc_profile(double z) {  // Eq. 7, zero for z >= 1
@@ -109,9 +167,38 @@ extern "C" rk_status rk_apply_K_noalloc(const rk_grid* grid, int32_t degree, dou
   long long tab_need = 0;
   for (int k = 0; k < 3; ++k) tab_need += (long long)(2 * degree + 1) * grid->n[k] + 2LL * grid->n[k];
   if (tab_need > kTableDoubles) return nf(RK_ERR_UNSUPPORTED, "tables exceed the fixed scratch");
+  for (int k = 0; k < 3; ++k)
+    if (grid->n[k] > kMaxSide) return nf(RK_ERR_UNSUPPORTED, "box side beyond the projection array");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nf(RK_ERR_CUDA, "cudaGetDevice failed");
+  const void* arrays[5] = {chi, chiV, b, d, f};
+  for (const void* p : arrays)
+    if (!device_array_ok(p, dev))
+      return nf(RK_ERR_INVALID_ARG, "arrays must be 16-byte aligned device memory of the current device");
   cudaStream_t st = (cudaStream_t)stream;
   double* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) return nf(RK_ERR_CUDA, "cudaGetSymbolAddress failed");
+  int* flags = nullptr;
+  uint8_t* proj = nullptr;
+  if (symbol_address(&base, g_noalloc_scratch) != cudaSuccess || symbol_address(&flags, g_noalloc_flags) != cudaSuccess ||
+      symbol_address(&proj, g_noalloc_proj) != cudaSuccess)
+    return nf(RK_ERR_CUDA, "cudaGetSymbolAddress failed");
+
+  // the gap of Eq. 66, checked on the device before anything else is queued
+  if (cudaMemsetAsync(flags, 0, 4 * sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(proj, 0, 3 * kMaxSide, st) != cudaSuccess)
+    return nf(RK_ERR_CUDA, "clearing the flags failed");
+  {
+    const long long blocks = std::min<long long>((nbox + 255) / 256, 4 * 152);
+    count_launch(2);
+    k_noalloc_project<<<(unsigned)blocks, 256, 0, st>>>(chi, grid->n[0], grid->n[1], grid->n[2], nbox, proj);
+    k_noalloc_gap<<<1, 32, 0, st>>>(proj, grid->n[0], grid->n[1], grid->n[2], reach, flags + 1);
+    int gap_bad = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&gap_bad, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return nf(RK_ERR_CUDA, "gap check failed");
+    if (gap_bad) return nf(RK_ERR_UNSUPPORTED, "gap of chi narrower than the support (Eq. 66)");
+  }
 
   // scratch layout: [tables | x outputs | y outputs | z outputs]
   double* coef[3];
@@ -152,6 +239,8 @@ extern "C" rk_status rk_apply_K_noalloc(const rk_grid* grid, int32_t degree, dou
   auto base_args = [&](int axis) {
     PassArgs<double> a;
     memset(&a, 0, sizeof(a));
+    a.err = flags;                 // a bounded wait that gives up sets flags[0]
+    a.coef_rows = degree + 1;      // the rows the table kernel fills
     a.coef = coef[axis];
     a.tw = tw[axis];
     a.nx = grid->n[0];
@@ -254,5 +343,8 @@ extern "C" rk_status rk_apply_K_noalloc(const rk_grid* grid, int32_t degree, dou
   }
   rx.g_begin[1] = nX;
   if (launch_merge<double>(0, grid->n[0], rx, st) != cudaSuccess) return nf(RK_ERR_CUDA, "x merge failed");
+  count_launch();
+  k_noalloc_poison<<<(unsigned)std::min<long long>((nbox + 255) / 256, 4 * 152), 256, 0, st>>>(f, nbox, flags);
+  if (cudaGetLastError() != cudaSuccess) return nf(RK_ERR_CUDA, "status kernel launch failed");
   return RK_OK;
 }

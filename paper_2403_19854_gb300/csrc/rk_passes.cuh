@@ -82,6 +82,9 @@ struct PassArgs {
   unsigned* counter;          // MERGE: blocks finished (the last one reduces and resets it)
   int* err;                   // set to 1 when a bounded wait for an input tile gave up
   int xbulk;                  // x passes: rows arrive by bulk async copies (set by the launcher)
+  int short_wait;             // 1: the first wait for each input tile gives up at once (tests
+                              // of the time-out path; the copy still lands before the block
+                              // returns); 0: waits of kWaitLimit polls
 };
 
 // ---------------------------------------------------------------- strided passes
@@ -216,16 +219,16 @@ struct TileFeed {
   }
   // wait for the tile; false (uniformly over the block) if the bounded wait gave up,
   // after which the caller returns
-  RK_DEV bool wait(int* err) {
+  RK_DEV bool wait(int* err, int short_wait) {
     bool ok = true;
     if (tma_axis) {
-      ok = mbar_wait(bar, phase);
+      ok = mbar_wait(bar, phase, short_wait ? 0u : kWaitLimit);
       phase ^= 1u;
     } else {
       cp_async_wait_all();
     }
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0 && err) atomicExch(err, 1);
+      if (threadIdx.x == 0) flag_wait_error(err);
       if (tma_axis) mbar_wait(bar, phase ^ 1u);  // the copy still in flight, bounded
       return false;
     }
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::M
     const long long base = x0 + (tile / nbx) * a.other_stride + 2 * l;
     const bool ok = x0 + 2 * l < a.nx;
     for (int g = 0; g < a.n_groups; ++g) {
-      if (!feed.wait(a.err)) return;  // (a block-wide barrier: the previous tile's flags are no longer read)
+      if (!feed.wait(a.err, a.short_wait)) return;  // (a block-wide barrier: the previous tile's flags are no longer read)
       if (PW > 0 && g == 0) {
         // the flag bytes of the tile rows: a row's ROW / 4 <= 8 groups start at bit
         // g0 = (tile origin + row * line_stride) / 4 and span at most two bytes (one
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(Strided<T, N, L>::THREADS, Strided<T, N, L>::M
       for (int r = 0; r < S::R; ++r) acc[r] = cmk((T)0, (T)0);
       for (int q = a.g_begin[g]; q < a.g_begin[g + 1]; ++q) {
         const int m = a.term_m[q];
-        if (!feed.wait(a.err)) return;
+        if (!feed.wait(a.err, a.short_wait)) return;
 #pragma unroll
         for (int r = 0; r < S::R; ++r) v[r] = S::at(feed.tile, F::nat_pos(t, r), l);
         RK_SYNC();
@@ -430,12 +433,12 @@ struct XFeed {
     }
   }
   // false (uniformly) when the bounded wait gave up; the caller returns
-  RK_DEV bool wait(int* err) {
-    const bool ok = mbar_wait(bar, phase);
+  RK_DEV bool wait(int* err, int short_wait) {
+    const bool ok = mbar_wait(bar, phase, short_wait ? 0u : kWaitLimit);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0 && err) atomicExch(err, 1);
-      mbar_wait(bar, phase ^ 1u);
+      if (threadIdx.x == 0) flag_wait_error(err);
+      mbar_wait(bar, phase ^ 1u);  // the copy still in flight, bounded
       return false;
     }
     return true;
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
     const long long nrows = (long long)a.ny * a.nz;
     const int rows = (int)((nrows - row0) < X::ROWS ? (nrows - row0) : X::ROWS);
     feed.issue(tileA, a.cg_r ? a.cg_r : a.in[a.g_io[0]], tileB, a.cg_r ? a.cg_p : nullptr, row0, rows);
-    if (!feed.wait(a.err)) return;
+    if (!feed.wait(a.err, a.short_wait)) return;
   }
   const T* ra = tileA + (2 * l) * X::PITCH;  // this thread's rows in the tiles
   const T* rb = ra + X::PITCH;

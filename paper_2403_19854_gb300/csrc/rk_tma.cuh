@@ -56,11 +56,21 @@ RK_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase `parity` of bar; false if the limit ran out.
-RK_DEV bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (unsigned i = 0; i < kWaitLimit; ++i)
+// Bounded wait for the phase `parity` of bar: at most `limit` polls; false if the
+// limit ran out.
+RK_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned limit = kWaitLimit) {
+  for (unsigned i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// Record that a bounded wait gave up: the error word is a mapped host word or a
+// device word; storing 1 is idempotent, so no atomic is needed.
+RK_DEV void flag_wait_error(int* err) {
+  if (err) {
+    *(volatile int*)err = 1;
+    __threadfence_system();
+  }
 }
 
 }  // namespace rk

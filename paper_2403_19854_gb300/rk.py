@@ -29,7 +29,7 @@ EXPORTED = ["rk_default_solve_opts", "rk_supported_length", "rk_setup", "rk_sing
             "rk_kernel_launches", "rk_profile_enable", "rk_profile_read", "rk_profile_class_name",
             "rk_solve_vjp", "rk_clone", "rk_solve_batched", "rk_apply_precond", "rk_boundary_rhs",
             "rk_solve_neumann", "rk_apply_M", "rk_lumped_mass", "rk_transient_explicit", "rk_transient_implicit",
-            "rk_nonlinear_force", "rk_solve_nonlinear"]
+            "rk_nonlinear_force", "rk_solve_nonlinear", "rk_debug_short_waits", "rk_apply_K_noalloc"]
 NONLINEARITIES = {"cubic": 0, "sinh": 1, "exp": 2}
 PROF_CLASSES = 12
 
@@ -117,6 +117,8 @@ def lib():
     L.rk_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]
     L.rk_profile_class_name.argtypes = [i32]
     L.rk_profile_class_name.restype = ctypes.c_char_p
+    L.rk_debug_short_waits.argtypes = [vp, i32]
+    L.rk_apply_K_noalloc.argtypes = [ctypes.POINTER(Grid), i32, f64, vp, vp, vp, vp, vp, vp]
     for name in EXPORTED:
         if getattr(L, name).restype is ctypes.c_int:  # default
             pass
@@ -306,6 +308,11 @@ class Handle:
         return tuple(n), s.value, nom.value
 
     # ---------------------------------------------------------- instrumentation
+    def debug_short_waits(self, enable=True):
+        """Diagnostic: make the first bounded wait for each input tile of the TMA-fed
+        passes give up at once (the next synchronising call reports RK_ERR_TIMEOUT)."""
+        _check(lib().rk_debug_short_waits(self._h, 1 if enable else 0))
+
     def profile(self, enable=True):
         """Start/stop per-kernel-class CUDA-event timing (counters cleared)."""
         _check(lib().rk_profile_enable(self._h, 1 if enable else 0))
