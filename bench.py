@@ -122,9 +122,9 @@ def aggregate_over_ranks(ms, units, world, device):
 
 # ------------------------------------------------------------------- oracle
 def oracle_kd_rate(n_box=64, a_tilde=2.5, reps=3):
-    """FP64 oracle matrix-free K.d (neighbour loops, one host core) on a bounded cube
-    sample; returns (DOF/s, sample description, seconds)."""
-    from oracle.oracle import Oracle
+    """FP64 oracle matrix-free K.d (neighbour loops on all host threads) on a bounded
+    cube sample; returns (DOF/s, sample description, seconds, threads)."""
+    from oracle.oracle import Oracle, threads
     from paper_2403_19854_gb300 import workloads as W
     p = W.cube_problem(n_box, a_tilde, 1, "sin")
     t0 = time.perf_counter()
@@ -136,10 +136,46 @@ def oracle_kd_rate(n_box=64, a_tilde=2.5, reps=3):
     for _ in range(reps):
         o.apply_K(p.V, d)
     dt = (time.perf_counter() - t0) / reps
-    desc = (f"oracle matrix-free K.d (FP64 neighbour loops, 1 thread) on the {n_box}^3-box unit cube "
+    nt = threads()
+    desc = (f"oracle matrix-free K.d (FP64 neighbour loops, {nt} host threads) on the {n_box}^3-box unit cube "
             f"({p.n_omega} DOF, a=2.5h, linear), mean of {reps} after 1 warm-up; shape-function build "
-            f"{tb:.1f} s excluded")
-    return p.n_omega / dt, desc, dt
+            f"{tb:.2f} s excluded")
+    return p.n_omega / dt, desc, dt, nt
+
+
+def oracle_timings():
+    """The traditional method's other costs on the host (all threads), each on the
+    largest cube the host handles in seconds: moment matrices, M^{-1} and shape
+    functions (64^3 box), CSR assembly of K (Eq. 26) and one CSR product (48^3),
+    and the full Dirichlet solve (assembly, f^r, CG on the CSR to 1e-10; 32^3)."""
+    from oracle.oracle import Oracle, threads
+    from paper_2403_19854_gb300 import workloads as W
+    out = {"threads": threads()}
+    p = W.cube_problem(64, 2.5, 1, "sin")
+    t0 = time.perf_counter()
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    out["moments_Minv_shape_functions_64"] = {"s": time.perf_counter() - t0, "dof": p.n_omega}
+    del o
+    p = W.cube_problem(48, 2.5, 1, "sin")
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    t0 = time.perf_counter()
+    nnz = o.assemble_K(p.V)
+    ta = time.perf_counter() - t0
+    x = W.random_field(p.nbox, 2) * p.chi
+    o.spmv(x)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        o.spmv(x)
+    out["assembly_48"] = {"s": ta, "dof": p.n_omega, "nnz": nnz}
+    out["csr_spmv_48"] = {"s": (time.perf_counter() - t0) / 3, "dof": p.n_omega, "nnz": nnz}
+    del o
+    p = W.cube_problem(32, 2.5, 1, "sin")
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    t0 = time.perf_counter()
+    _, info = o.solve(p.V, p.chi_gamma, p.r, p.g, tol=1e-10)
+    out["dirichlet_solve_32"] = {"s": time.perf_counter() - t0, "dof": p.n_omega, "cg_iterations": info["iterations"],
+                                 "rel_residual": info["rel_residual"]}
+    return out
 
 
 def run_reference(args):
@@ -148,20 +184,55 @@ def run_reference(args):
         return 0
     vals = []
     desc = ""
+    nt = 1
     t_all = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        v, desc, dt = oracle_kd_rate(reps=1)
+        v, desc, dt, nt = oracle_kd_rate(reps=1)
         if i >= args.warmup:
             vals.append(v)
     elapsed = time.perf_counter() - t_all
     value = statistics.mean(vals)
+    timings = oracle_timings()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / (args.warmup + args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "cube256-linear-a2.5-sin (oracle on a bounded 64^3-box sample)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": desc},
+            "oracle_timings": timings,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ku(args):
+    """K.u alone, for external profilers: set-up on a cube box, then --reps stiffness
+    actions (Alg. 2).  Box sides a x b x c (--box 256x256x128) embed the cube domain
+    of the smallest side in a larger box, which keeps the kernels of the long axes
+    while holding less device memory.  Prints the device memory held and a checksum."""
+    import torch
+    from paper_2403_19854_gb300 import rk
+    from paper_2403_19854_gb300 import workloads as W
+    box = tuple(int(v) for v in args.box.split("x"))
+    if len(box) == 1:
+        box = box * 3
+    at = 2.5 if args.degree == 1 else 3.0
+    p = W.cube_problem(min(box), at, args.degree, "zero")
+    if box != p.n:
+        p = W.embed(p, box)
+    dev = torch.device("cuda:0")
+    H = rk.Handle.from_problem(p, device=dev)
+    dt = torch.float32 if args.dtype == "f32" else torch.float64
+    g = torch.Generator(device=dev)
+    g.manual_seed(20240328)
+    x = torch.rand(p.nbox, dtype=dt, device=dev, generator=g)
+    y = torch.empty_like(x)
+    for _ in range(args.reps):
+        H.apply_K(x, y)
+    torch.cuda.synchronize()
+    free, total = torch.cuda.mem_get_info()
+    print(f"box {box} degree {args.degree} {args.dtype}: {args.reps} K.u, checksum {float(y.abs().sum()):.6e}, "
+          f"device memory {total - free:.3e} B in use")
+    H.close()
     return 0
 
 
@@ -288,9 +359,9 @@ def run_ours(args):
     L1 = rk.kernel_launches()
     clocks = clk.stop()
     ms_local = e0.elapsed_time(e1)
-    # one more step with CUDA events around every kernel class on the launching
-    # stream (this disables the graph replay of CG chunks, so it is kept out of
-    # the timed steps): per-kernel durations for the roofline
+    # one more step, not timed, with CUDA events around every kernel class on the
+    # launching stream (this disables the graph replay of CG chunks): per-kernel
+    # durations for the roofline
     p0 = torch.cuda.Event(enable_timing=True)
     p1 = torch.cuda.Event(enable_timing=True)
     p0.record(stream)
@@ -304,7 +375,7 @@ def run_ours(args):
     value = units / (ms / 1e3)
     u_mixed = u.cpu().numpy().copy()
 
-    # kernel profile over the timed steps: dominant class and its roofline
+    # kernel profile of the profiled step: dominant class and its roofline
     agg = {}
     for pr in profs:
         for k, (t_ms, n) in pr.items():
@@ -377,8 +448,9 @@ def run_ours(args):
     del qa, Aw, v64, f_out, v32, f32, dd
 
     # the embedded-domain workload at full size: 12 spheres in a 256^3 box,
-    # quadratic basis, a = 3h (set-up and K.u; its solves do not converge, see the
-    # design notes on DNI with the quadratic basis)
+    # quadratic basis, a = 3h (set-up and K.u; with direct nodal integration the
+    # quadratic-basis stiffness matrix has near-null oscillatory modes, kappa above
+    # 1e8 already at 24^3, so its solves do not reach 1e-10)
     sph = W.spheres_problem(n_box=args.size, n_spheres=12, a_tilde=3.0, degree=2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -470,7 +542,7 @@ def run_ours(args):
     hu = torch.empty(p.nbox, dtype=torch.float64).pin_memory()
     e2e_ms = []
     e2e_mv = 0
-    for i in range(max(1, min(args.steps, 2))):
+    for i in range(max(1, args.steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         H = rk.Handle(p.n, p.h, hp["chi"], hp["chi_gamma"], hp["V"], 1, 2.5, stream=rk.ctypes.c_void_p(stream.cuda_stream))
@@ -486,8 +558,8 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, desc, _ = oracle_kd_rate()
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        v, desc, _, nt = oracle_kd_rate()
+        cpu = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": desc}
 
     if rank == 0:
         m = p.chi > 0
@@ -626,8 +698,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=0.0,
                     help="ncu dram bytes per launch of the dominant kernel (from profiles/), if measured")
-    ap.add_argument("--workload", default="cube", choices=["cube", "batched"],
-                    help="cube: the 256^3 cube solve (default); batched: uneven embedded domains")
+    ap.add_argument("--workload", default="cube", choices=["cube", "batched", "ku"],
+                    help="cube: the 256^3 cube solve (default); batched: uneven embedded domains; "
+                         "ku: set-up and --reps K.u on --box (for external profilers)")
+    ap.add_argument("--box", default="128", help="ku: box sides, n or a x b x c")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="ku: precision of K.u")
+    ap.add_argument("--degree", type=int, default=1, choices=[1, 2], help="ku: basis degree")
+    ap.add_argument("--reps", type=int, default=4, help="ku: number of K.u")
     ap.add_argument("--domains", type=int, default=64, help="batched: number of domains")
     ap.add_argument("--max-iter", type=int, default=2000, help="batched: CG iterations per item")
     ap.add_argument("--precond", default="none", choices=["none", "spectral"], help="batched: preconditioner")
@@ -636,6 +713,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "ku":
+        return run_ku(args)
     return run_ours(args)
 
 

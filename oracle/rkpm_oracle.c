@@ -17,7 +17,7 @@
  * exist for this method.  The grid is NOT periodic: a neighbour must lie inside
  * the grid.
  *
- * Readings of the paper used here (each is listed in the design notes):
+ * Readings of the paper used here:
  *  - Eq. 7 at z >= 1 is taken as exactly 0, and its second branch is evaluated
  *    in the factored form (4/3)(1-z)^3 (same polynomial).  A node at distance
  *    exactly a is therefore not a neighbour.
