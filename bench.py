@@ -241,18 +241,16 @@ def run_ku(args):
 # iteration (linear basis s = 4, w = bytes per real, u8 masks, int32 node index):
 #   x_split       p_old, r in; p, 2 fields out  (direction update fused, no input mask)
 #   y_split       2 in, 3 out
-#   z_split       3 in, s out (with the pointwise stage of the regular nodes when n_x % 4 == 0:
-#                 its scaled outputs are their g, plus 2 bits per 4 nodes, not counted)
-#   stiff_pointwise  s in, s out, node index: every node when n_x % 4 != 0; otherwise only
-#                 the boundary nodes the z split leaves (no per-box-node figure)
-#   z_merge       s in, 3 out
+#   z_merge       the z axis of Alg. 2 as its regular part: the 3 y outputs in, the 3
+#                 z outputs out (one spectral multiplier per group)
+#   stiff_pointwise  the local corrections of the non-regular nodes along z (reads and
+#                 updates the fields on the boundary layers only: no per-box-node figure)
 #   y_merge       3 in, 2 out
 #   x_merge       2 in + output mask, Ap out, p in (p.Ap fused)
 #   cg_vector     x, r, p, Ap in; x, r out
-def pass_bytes(cls, w, s=4, fused=True):
-    return {"x_split": 5 * w, "y_split": 5 * w, "z_split": (3 + s) * w,
-            "stiff_pointwise": None if fused else 2 * s * w + 4,
-            "z_merge": (s + 3) * w, "y_merge": 5 * w, "x_merge": 4 * w + 1, "cg_vector": 6 * w}.get(cls)
+def pass_bytes(cls, w, s=4):
+    return {"x_split": 5 * w, "y_split": 5 * w, "z_merge": 6 * w, "y_merge": 5 * w, "x_merge": 4 * w + 1,
+            "cg_vector": 6 * w}.get(cls)
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
@@ -387,7 +385,7 @@ def run_ours(args):
     (dname, dprec), (dms, dn) = dom
     w = 8 if dprec == "f64" else 4
     peak, peak_kind = _peaks()
-    bpn = pass_bytes(dname, w, fused=p.n[0] % 4 == 0)
+    bpn = pass_bytes(dname, w)
     roofline = None
     if bpn is not None:
         traffic = args.traffic_bytes if args.traffic_bytes > 0 else measured_traffic(dname, dprec, args.size)

@@ -162,6 +162,17 @@ struct rk_handle {
   int zrow_scaled[3] = {-1, -1, -1};
   int zrows = 0;
   double inv_c[3] = {0.0, 0.0, 0.0};
+  // z axis of Alg. 2 as its regular part plus local corrections (rk_zcorr.cuh):
+  // zreg_row[g] is the row of the z table holding c n |T^|^2 for group g (-1: the
+  // group has no gradient basis function, its regular part is 0); zwin lists the
+  // correction windows
+  bool zcorr = false;
+  int zreg_row[kMaxIn];
+  ZWin* zwin = nullptr;
+  long long nzwin = 0;
+  uint32_t* zbits = nullptr;  // per z-line: need bits (8 words), then marked bits (8 words per line)
+  double ztab[3][2 * kZMaxReach + 1] = {};  // T_m(o) along z, m <= degree
+  double creg[10] = {};                     // c_p of a regular node
   // workspaces of the operator chains: X outputs, Y outputs, z-pass outputs
   double* ws64 = nullptr;
   float* ws32 = nullptr;
@@ -561,6 +572,9 @@ PointwiseArgs<T> pointwise_base(const rk_handle* h) {
 }
 
 template <typename T>
+ZCorrArgs<T> zcorr_args(const rk_handle* h);
+
+template <typename T>
 rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uint8_t* out_mask, cudaStream_t s,
                const CGFuse<T>* fuse = nullptr) {
   const Chain& c = h->chain;
@@ -593,6 +607,34 @@ rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uin
     }
   }
   az.g_begin[c.nY] = q;
+  if (h->zcorr) {
+    // the z axis as its regular part -- one spectral pass, E_g -> G_g with the
+    // multiplier c n |T^|^2 of the group's gradient basis function (none: G_g = 0)
+    // -- and the local corrections of the non-regular nodes (rk_zcorr.cuh)
+    PassArgs<T> rg = pass_base<T>(h, 2);
+    rg.coef_rows = h->zrows;
+    rg.n_groups = c.nY;
+    int nt = 0;
+    for (int g = 0; g < c.nY; ++g) {
+      rg.in[g] = h->ws<T>(c.nX + g);
+      rg.out[g] = h->ws<T>(c.nX + c.nY + g);
+      rg.g_io[g] = g;
+      rg.g_begin[g] = nt;
+      if (h->zreg_row[g] >= 0) {
+        rg.term_io[nt] = g;
+        rg.term_m[nt] = h->zreg_row[g];
+        ++nt;
+      }
+    }
+    rg.g_begin[c.nY] = nt;
+    RK_TRY(run_merge<T>(h, 2, rg, s));
+    {
+      ProfScope ps(h, prof_cls<T>(RK_PROF_Z_STIFF), s);
+      cudaError_t e = launch_zcorr<T>(zcorr_args<T>(h), s);
+      if (e != cudaSuccess) return cuda_fail(e, "z corrections");
+    }
+    return chain_reflect_yx<T>(h, f, out_mask, s, fuse);
+  }
   PointwiseArgs<T> pw = pointwise_base<T>(h);
   for (int p = 0; p < h->s; ++p) pw.D[p] = h->ws<T>(dbase + p);
   if (h->n[0] % 4 == 0 && h->diag_reg) {
@@ -1755,11 +1797,37 @@ rk_status scale_regular_rows(rk_handle* h, cudaStream_t s) {
     c[k] = h->breg64[3 * S] * h->breg64[k * S + 1 + k] * h->breg64[k * S + 1 + k];
     h->inv_c[k] = 1.0 / c[k];
   }
+  // rows of the regular part of the z axis (rk_zcorr.cuh): for the group holding
+  // the gradient basis function p = 1 + k, the multiplier c_k n |T^_{alpha_z(p)}|^2
+  // of the forward and the reflected convolution with the pointwise factor c_k
+  // between them (coef holds T^/n; the inverse transform in between is unnormalised)
+  const Chain& ch = h->chain;
+  for (int g = 0; g < ch.nY; ++g) {
+    h->zreg_row[g] = -1;
+    for (auto& t : ch.zterms[g])
+      if (t.second >= 1 && t.second <= 3) {
+        h->zreg_row[g] = next[0];
+        next[0] += 2;
+        rows = std::max(rows, h->zreg_row[g] + 1);
+      }
+  }
   coef.resize((size_t)rows * n, 0.0);
   for (int k = 0; k < 3; ++k) {
     const int mz = h->chain.alpha[1 + k][2];
     for (int i = 0; i < n; ++i) coef[(size_t)h->zrow_scaled[k] * n + i] = c[k] * coef[(size_t)mz * n + i];
   }
+  for (int g = 0; g < ch.nY; ++g) {
+    if (h->zreg_row[g] < 0) continue;
+    for (auto& t : ch.zterms[g])
+      if (t.second >= 1 && t.second <= 3) {
+        const int k = t.second - 1, mz = t.first;
+        for (int i = 0; i < n; ++i) {
+          const double cm = coef[(size_t)mz * n + i];
+          coef[(size_t)h->zreg_row[g] * n + i] = c[k] * (double)n * cm * cm;
+        }
+      }
+  }
+  for (int p = 0; p < S; ++p) h->creg[p] = (p >= 1 && p <= 3) ? c[p - 1] : 0.0;
   std::vector<float> coef32(coef.begin(), coef.end());
   rk_status st;
   if ((st = h->alloc(&h->coef64[2], coef.size())) != RK_OK || (st = h->alloc(&h->coef32[2], coef.size())) != RK_OK)
@@ -1795,6 +1863,99 @@ rk_status scale_regular_rows(rk_handle* h, cudaStream_t s) {
   h->zrows = rows;
   h->diag_reg = h->regbits != nullptr;
   return RK_OK;
+}
+
+// The z axis of Alg. 2 as its regular part plus local corrections (rk_zcorr.cuh):
+// the correction windows of every z-line -- the positions within the reach of a
+// node that is not regular but lies within the support of chi (box dilation of chi
+// by the reach) -- and the real-space z tables T_m(o).  Needs the regular rows of
+// scale_regular_rows; leaves h->zcorr false (the z axis then runs as split,
+// pointwise stage and merge) for 2D boxes, boxes without regular nodes and
+// supports or sides beyond the window kernel's limits.
+rk_status build_zwindows(rk_handle* h, cudaStream_t s) {
+  h->zcorr = false;
+  if (h->dim != 3 || !h->diag_reg || h->n[2] > 256 || h->reach < 1 || h->reach > kZMaxReach) return RK_OK;
+  // the kernel's compile-time basis structure must be the handle's
+  const Chain& ch = h->chain;
+  for (int g = 0; g < ch.nY; ++g)
+    for (auto& t : ch.zterms[g]) {
+      const int p = t.second;
+      const bool ok = h->s == 4 ? (ZBasis<4>::grp(p) == g && ZBasis<4>::az(p) == t.first)
+                                : (ZBasis<10>::grp(p) == g && ZBasis<10>::az(p) == t.first);
+      if (!ok) return RK_OK;
+    }
+  const long long n = h->nbox;
+  const long long nl = (long long)h->n[0] * h->n[1];
+  const long long ng = (long long)((h->n[0] + kZGW - 1) / kZGW) * h->n[1];
+  uint8_t* tmp = nullptr;
+  int* counts = nullptr;
+  if (!h->zbits) RK_TRY(h->alloc(&h->zbits, (size_t)16 * nl));
+  uint32_t* nk = h->zbits;
+  uint32_t* mk = h->zbits + (size_t)8 * nl;
+  cudaError_t e = cudaMalloc((void**)&tmp, (size_t)3 * n + (size_t)nl);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&counts, sizeof(int) * ((size_t)ng + 1));
+  auto done = [&](rk_status st) {
+    cudaFree(tmp);
+    cudaFree(counts);
+    return st;
+  };
+  if (e != cudaSuccess) return done(cuda_fail(e, "window workspace"));
+  uint8_t *a = tmp, *b = tmp + n, *need = tmp + 2 * n, *flags = tmp + 3 * n;
+  // box dilation of chi by the reach = complement of the erosion of its complement
+  if ((e = launch_u8_not(a, h->chi, n, s)) != cudaSuccess || (e = launch_erode(b, a, 0, h->reach, h->n, s)) != cudaSuccess ||
+      (e = launch_erode(a, b, 1, h->reach, h->n, s)) != cudaSuccess ||
+      (e = launch_erode(b, a, 2, h->reach, h->n, s)) != cudaSuccess || (e = launch_u8_not(a, b, n, s)) != cudaSuccess ||
+      (e = launch_zwin_need(need, a, h->cidx, n, s)) != cudaSuccess ||
+      (e = launch_zwin_mark(need, h->chi, h->n, h->reach, mk, nk, flags, s)) != cudaSuccess)
+    return done(cuda_fail(e, "correction nodes"));
+  int total = 0;
+  const int chunk = zcorr_chunk(h->s);
+  if ((e = launch_zwin_groups(0, mk, flags, h->n, chunk, counts, nullptr, s)) != cudaSuccess ||
+      (e = launch_scan_counts(counts, (int)ng, counts + ng, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&total, counts + ng, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return done(cuda_fail(e, "correction windows"));
+  rk_status st = h->alloc(&h->zwin, (size_t)std::max(total, 1));
+  if (st != RK_OK) return done(st);
+  if ((e = launch_zwin_groups(1, mk, flags, h->n, chunk, counts, h->zwin, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return done(cuda_fail(e, "correction windows"));
+  h->nzwin = total;
+  for (int m = 0; m <= h->degree; ++m)
+    for (int o = -h->reach; o <= h->reach; ++o) {
+      const double xi = (double)o / h->a_tilde;
+      h->ztab[m][o + h->reach] = std::pow(xi, m) * kernel_profile(xi);
+    }
+  h->zcorr = true;
+  return done(RK_OK);
+}
+
+template <typename T>
+ZCorrArgs<T> zcorr_args(const rk_handle* hc) {
+  rk_handle* h = const_cast<rk_handle*>(hc);  // the workspace fields are written through
+  ZCorrArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  const Chain& c = h->chain;
+  a.nY = c.nY;
+  a.s = h->s;
+  for (int g = 0; g < c.nY; ++g) {
+    a.E[g] = h->ws<T>(c.nX + g);
+    a.G[g] = h->ws<T>(c.nX + c.nY + g);
+  }
+  a.cidx = h->cidx;
+  a.ctab = ctab_of<T>(h);
+  for (int p = 0; p < h->s; ++p) a.creg[p] = (T)h->creg[p];
+  for (int m = 0; m <= h->degree; ++m)
+    for (int j = 0; j <= 2 * h->reach; ++j) a.tab[m][j] = (T)h->ztab[m][j];  // rows of length 2r + 1
+  a.r = h->reach;
+  a.nx = h->n[0];
+  a.ny = h->n[1];
+  a.nz = h->n[2];
+  a.win = h->zwin;
+  a.nwin = h->nzwin;
+  a.nbits = h->zbits;
+  a.mbits = h->zbits + (size_t)8 * h->n[0] * h->n[1];
+  return a;
 }
 
 // Vector-Jacobian product of the solve map (r, g) -> u^h for a cotangent e on the
@@ -2143,6 +2304,7 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
   if (st != RK_OK) return bail(st);
   if ((st = compress_coefficients(h, s)) != RK_OK) return bail(st);
   if ((st = scale_regular_rows(h, s)) != RK_OK) return bail(st);
+  if ((st = build_zwindows(h, s)) != RK_OK) return bail(st);
   *out = h;
   if (h->n_singular)
     return fail(RK_ERR_SINGULAR_MOMENT,

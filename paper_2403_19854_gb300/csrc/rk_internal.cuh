@@ -8,6 +8,7 @@
 
 #include "rk_passes.cuh"
 #include "rk_precond.cuh"
+#include "rk_zcorr.cuh"
 
 namespace rk {
 
@@ -99,6 +100,22 @@ cudaError_t launch_transpose_u_fields(T* const* D, const T* y, const T* b0, int 
 // the pointwise stage on the listed 4-node groups only (after a z SPLIT with diag)
 template <typename T>
 cudaError_t launch_pointwise_groups(const PointwiseArgs<T>& a, const int* list, long long count, cudaStream_t s);
+
+// ------------------------------------- z axis: regular part + local corrections
+// G_g += reflected z-convolutions of delta over the correction windows (rk_zcorr.cuh)
+template <typename T>
+cudaError_t launch_zcorr(const ZCorrArgs<T>& a, cudaStream_t s);
+// need = dil && cidx != 0;  out = !in
+cudaError_t launch_zwin_need(uint8_t* need, const uint8_t* dil, const int* cidx, long long n, cudaStream_t s);
+cudaError_t launch_u8_not(uint8_t* out, const uint8_t* in, long long n, cudaStream_t s);
+// per z-line need nodes and the positions within r of one (8 words per line each),
+// and flags (1: chi node, 2: need node)
+cudaError_t launch_zwin_mark(const uint8_t* need, const uint8_t* chi, const int n[3], int r, uint32_t* mk,
+                             uint32_t* nk, uint8_t* flags, cudaStream_t s);
+// records per group of kZGW lines: fill = 0 counts them into counts[group]; fill = 1
+// writes them from the exclusive offsets in counts
+cudaError_t launch_zwin_groups(int fill, const uint32_t* mk, const uint8_t* flags, const int n[3], int chunk,
+                               int* counts, ZWin* out, cudaStream_t s);
 
 // ------------------------------------------------------------ CG kernels
 

@@ -247,6 +247,114 @@ cudaError_t launch_gather(double* out, const double* src, long long stride, long
 }
 
 // up to 10 field pointers by value (kernel arguments)
+// ------------------------------------- z axis: regular part + local corrections
+template <typename T, int S, int R>
+cudaError_t zcorr_sr(const ZCorrArgs<T>& a, cudaStream_t s) {
+  constexpr int W = zcorr_warps<T, S>();  // records (warps) per block
+  const long long nb = (a.nwin + W - 1) / W;
+  const unsigned grid = (unsigned)(nb < 152 * 32 ? nb : 152 * 32);
+  count_launch();
+  k_zcorr<T, S, R, W><<<grid, 32 * W, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, int S>
+cudaError_t zcorr_s(const ZCorrArgs<T>& a, cudaStream_t s) {
+  switch (a.r) {
+    case 1: return zcorr_sr<T, S, 1>(a, s);
+    case 2: return zcorr_sr<T, S, 2>(a, s);
+    case 3: return zcorr_sr<T, S, 3>(a, s);
+    case 4: return zcorr_sr<T, S, 4>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T>
+cudaError_t launch_zcorr(const ZCorrArgs<T>& a, cudaStream_t s) {
+  if (a.nwin <= 0) return cudaSuccess;
+  return a.s == 4 ? zcorr_s<T, 4>(a, s) : zcorr_s<T, 10>(a, s);
+}
+template cudaError_t launch_zcorr<float>(const ZCorrArgs<float>&, cudaStream_t);
+template cudaError_t launch_zcorr<double>(const ZCorrArgs<double>&, cudaStream_t);
+
+// need[i] = 1 where delta may be nonzero: a node that is not regular (cidx != 0)
+// within the support of some chi node (dil[i] = 1: box dilation of chi by r).
+__global__ void k_zwin_need(uint8_t* need, const uint8_t* dil, const int* cidx, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    need[i] = (dil[i] && cidx[i] != 0) ? 1 : 0;
+}
+
+// out[i] = 1 - in[i]
+__global__ void k_u8_not(uint8_t* out, const uint8_t* in, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = in[i] ? 0 : 1;
+}
+
+cudaError_t launch_zwin_need(uint8_t* need, const uint8_t* dil, const int* cidx, long long n, cudaStream_t s) {
+  const long long nb = (n + 255) / 256;
+  count_launch();
+  k_zwin_need<<<(unsigned)(nb < 152 * 32 ? nb : 152 * 32), 256, 0, s>>>(need, dil, cidx, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_u8_not(uint8_t* out, const uint8_t* in, long long n, cudaStream_t s) {
+  const long long nb = (n + 255) / 256;
+  count_launch();
+  k_u8_not<<<(unsigned)(nb < 152 * 32 ? nb : 152 * 32), 256, 0, s>>>(out, in, n);
+  return cudaGetLastError();
+}
+// Per z-line: nk[8 * line ..] = its `need` nodes (bit z), mk[8 * line ..] = the
+// positions within r (circularly) of one, flags[line] = 1 (has a chi node) | 2 (has
+// a need node).
+__global__ void k_zwin_mark(const uint8_t* need, const uint8_t* chi, int nx, int ny, int nz, int r, uint32_t* mk,
+                            uint32_t* nk, uint8_t* flags) {
+  const long long nlines = (long long)nx * ny;
+  for (long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x; L < nlines; L += (long long)gridDim.x * blockDim.x) {
+    uint32_t nb[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // n_z <= 256
+    bool any_need = false, any_chi = false;
+    for (int z = 0; z < nz; ++z) {
+      const long long i = L + (long long)z * nlines;
+      if (need[i]) {
+        nb[z >> 5] |= 1u << (z & 31);
+        any_need = true;
+      }
+      any_chi |= chi[i] != 0;
+    }
+    uint32_t m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (any_need)
+      for (int z = 0; z < nz; ++z) {
+        bool hit = false;
+        for (int o = -r; o <= r && !hit; ++o) {
+          int zz = z + o;
+          zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+          hit = (nb[zz >> 5] >> (zz & 31)) & 1u;
+        }
+        if (hit) m[z >> 5] |= 1u << (z & 31);
+      }
+    for (int k = 0; k < 8; ++k) {
+      mk[8 * L + k] = m[k];
+      nk[8 * L + k] = nb[k];
+    }
+    flags[L] = (any_chi ? 1 : 0) | (any_need ? 2 : 0);
+  }
+}
+
+cudaError_t launch_zwin_mark(const uint8_t* need, const uint8_t* chi, const int n[3], int r, uint32_t* mk,
+                             uint32_t* nk, uint8_t* flags, cudaStream_t s) {
+  const long long nl = (long long)n[0] * n[1];
+  count_launch();
+  k_zwin_mark<<<(unsigned)((nl + 127) / 128), 128, 0, s>>>(need, chi, n[0], n[1], n[2], r, mk, nk, flags);
+  return cudaGetLastError();
+}
+cudaError_t launch_zwin_groups(int fill, const uint32_t* mk, const uint8_t* flags, const int n[3], int chunk,
+                               int* counts, ZWin* out, cudaStream_t s) {
+  const long long ng = (long long)((n[0] + kZGW - 1) / kZGW) * n[1];
+  const unsigned grid = (unsigned)((ng + 127) / 128);
+  count_launch();
+  if (fill)
+    k_zwin_groups<true><<<grid, 128, 0, s>>>(mk, flags, n[0], n[1], n[2], chunk, counts, out);
+  else
+    k_zwin_groups<false><<<grid, 128, 0, s>>>(mk, flags, n[0], n[1], n[2], chunk, counts, out);
+  return cudaGetLastError();
+}
+
 template <typename T>
 struct DPtrs {
   T* p[10];
