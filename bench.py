@@ -663,6 +663,10 @@ def run_batched(args):
         rel = dd.pop("rel")
         dd["median_rel_residual"] = float(np.median(rel))
         dd["worst_rel_residual"] = float(np.max(rel))
+    max_it = max(i["iterations"] for i in infos)
+    launch_stats = {"gpu_launches_per_step": int((L1 - L0) / args.steps),
+                    "launches_per_cg_iteration_of_the_batch": (L1 - L0) / args.steps / max(max_it, 1),
+                    "max_iterations": int(max_it)}
     if rank == 0:
         sides = sorted({(it["S"], it["p"].n[0]) for it in items})
         line = {"metric": "batched DOF x K.u applications per second (uneven domains, mixed precision)",
@@ -675,7 +679,8 @@ def run_batched(args):
                            "box_nodes": int(sum(it["p"].nbox for it in items)),
                            "dof": int(sum(it["p"].n_omega for it in items)),
                            "padded_sides": [list(v) for v in sides]},
-                "per_degree": per_deg, "clocks": clocks, "gpu_launches": int(L1 - L0)}
+                "per_degree": per_deg, "launch_groups": launch_stats, "clocks": clocks,
+                "gpu_launches": int(L1 - L0)}
         print(json.dumps(line), flush=True)
     for hs in handles:
         for h in hs[1:]:

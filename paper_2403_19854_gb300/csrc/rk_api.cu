@@ -1053,6 +1053,11 @@ rk_status apply_precond(rk_handle* h, const T* r, T* z, cudaStream_t s, int rz_m
   if (!mult) {
     RK_TRY(owner->alloc(&mult, (size_t)owner->nxp * h->n[1] * h->n[2]));
     RK_CK(launch_symbol_table<T>(owner->sym64, mult, owner->nxp, h->n[1], h->n[2], s));
+    // finished before any stream uses it: clones of the owner share the table and
+    // may run on other streams (rk_solve_batched)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    RK_CK(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone) RK_CK(cudaStreamSynchronize(s));
   }
   pz.mult = mult;
   if (e == cudaSuccess) e = launch_pfft<T>(PF_SYM, h->n[2], pz, s);
