@@ -93,6 +93,7 @@ def _load():
     lib.orc_rhs.argtypes = [ctypes.c_void_p, _f64p, _f64p, _f64p]
     lib.orc_eval_u.argtypes = [ctypes.c_void_p, _f64p, _f64p]
     lib.orc_eval_u_transpose.argtypes = [ctypes.c_void_p, _f64p, _f64p]
+    lib.orc_grad_transpose.argtypes = [ctypes.c_void_p, _f64p, _f64p, _f64p]
     lib.orc_assemble_K.restype = ctypes.c_int64
     lib.orc_assemble_K.argtypes = [ctypes.c_void_p, _f64p]
     lib.orc_get_K.argtypes = [ctypes.c_void_p, _i64p, _i64p, _f64p]
@@ -244,6 +245,16 @@ class Oracle:
         w = np.zeros(self.nbox)
         _load().orc_eval_u_transpose(self._h, pe, w.ctypes.data_as(_f64p))
         return w
+
+    def grad_transpose(self, V, N) -> np.ndarray:
+        """Gradient-type nonlinear force (Eq. B.6-B.8, DNI): f_J = sum_S V_S
+        sum_k Psi^{grad k}_J(x_S) N^k_S, i.e. B^T N; N has shape (3, nbox)
+        (rows beyond the grid's dimension are ignored by the zero gradients)."""
+        V, pV = _f64(np.asarray(V).reshape(-1))
+        N, pN = _f64(np.asarray(N, dtype=np.float64).reshape(3, -1))
+        f = np.zeros(self.nbox)
+        _load().orc_grad_transpose(self._h, pV, pN, f.ctypes.data_as(_f64p))
+        return f
 
     def assemble_K(self, V):
         """Assemble K (Eq. 26 with direct nodal integration) as CSR over node numbers."""

@@ -619,6 +619,29 @@ void orc_eval_u_transpose(const orc_ctx *c, const double *e, double *w) {
   }
 }
 
+/* Gradient-type nonlinear force (Eq. B.6-B.8 with DNI): f_J = sum_S V_S sum_k
+   Psi^{grad k}_J(x_S) N^k_S over the quadrature nodes S whose support holds J,
+   i.e. B^T applied to the field of vectors N (three box fields, N^k at offset
+   k*nbox; V box-indexed).  Gathered per J; zero outside chi. */
+void orc_grad_transpose(const orc_ctx *c, const double *V, const double *N, double *f) {
+  const int ns = c->g.nslot;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < c->nbox; ++i) f[i] = 0.0;
+#pragma omp parallel for schedule(static)
+  for (int64_t J = 0; J < c->nnode; ++J) {
+    double acc = 0.0;
+    for (int sl = 0; sl < ns; ++sl) {
+      int tJ;
+      const int64_t S = covering_node(c, J, sl, &tJ);
+      if (S < 0) continue;
+      const int64_t bs = c->node_box[S];
+      const double *g = c->dpsi + ((size_t)S * ns + tJ) * 3;
+      acc += V[bs] * (g[0] * N[bs] + g[1] * N[c->nbox + bs] + g[2] * N[2 * c->nbox + bs]);
+    }
+    f[c->node_box[J]] = acc;
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Assembled stiffness matrix (Eq. 26 with DNI), CSR over node numbers       */
 /* ------------------------------------------------------------------------ */

@@ -294,6 +294,35 @@ def test_rhs_moments():
 
 
 @pytest.mark.parametrize("deg,a", [(1, 2.5), (2, 3.0)])
+def test_grad_force_moments(deg, a):
+    """The gradient-type nonlinear force of Eq. B.6-B.8, f_J = sum_S V_S sum_k
+    Psi^{grad k}_J(x_S) N^k_S, against the reproduction of gradients
+    (sum_J Psi^{grad k}_J(x) m(x_J) = d_k m(x) for monomials |m| <= n):
+    sum_J f_J m(x_J) = sum_S V_S sum_k N^k_S d_k m(x_S).  A transposed Psi
+    (Psi_S at x_J), a dropped component or a sign flips it."""
+    p = W.spheres_problem(n_box=16, n_spheres=3, a_tilde=a, degree=deg, r_range=(0.2, 0.3), seed=6)
+    o = Oracle(p.n, p.h, a, deg, p.chi)
+    rng = np.random.default_rng(17)
+    N = rng.standard_normal((3, p.nbox)) * p.chi
+    f = o.grad_transpose(p.V, N)
+    assert np.all(f[p.chi == 0] == 0.0)
+    X = _coords(p)
+    for al in _monomials(deg):
+        mono = X[:, 0] ** al[0] * X[:, 1] ** al[1] * X[:, 2] ** al[2]
+        rhs = 0.0
+        for k in range(3):
+            if al[k] == 0:
+                continue
+            e = list(al)
+            e[k] -= 1
+            dmono = al[k] * X[:, 0] ** e[0] * X[:, 1] ** e[1] * X[:, 2] ** e[2]
+            rhs += float((p.V * p.chi * N[k]) @ dmono)
+        lhs = float(f @ mono)
+        scale = float(np.abs(p.V * N).sum()) + 1e-300
+        assert abs(lhs - rhs) <= 1e-12 * scale, (al, lhs, rhs)
+
+
+@pytest.mark.parametrize("deg,a", [(1, 2.5), (2, 3.0)])
 def test_eval_u_reproduces_polynomials(deg, a):
     """u^h of Eq. 62 with d = a polynomial of degree <= n returns that polynomial at every
     node (near boundaries too)."""
