@@ -271,6 +271,18 @@ rk_status rk_transient_implicit(rk_handle* h, const double* f, const double* g, 
  */
 typedef enum rk_nonlinearity { RK_NL_CUBIC = 0, RK_NL_SINH = 1, RK_NL_EXP = 2 } rk_nonlinearity;
 rk_status rk_nonlinear_force(rk_handle* h, const double* d, int32_t kind, double c, double* fN, void* stream);
+/*
+ * rk_nonlinear_grad_force -- the gradient-type nonlinear force of Eq. B.5-B.8 in
+ * the form of Eq. B.10: f^N = B^T N with N^k(x) = a_k N(u^h(x)), i.e.
+ * f^N_I = chi_I sum_S chi_S V_S sum_k b^k_p(x_S) a_k N(u^h(x_S)) Hbar^a_p(x_I - x_S)
+ * (sum over p), evaluated as u^h (Alg. 3), the fields g_p = chi V sum_k a_k b^k_p N,
+ * and the reflected passes of Alg. 2.  N is the pointwise nonlinearity kind with
+ * coefficient c (as rk_nonlinear_force); a[3] (host) is the fixed direction of the
+ * vector nonlinearity (a[2] is ignored on a 2D box).  d, fN: [nbox], FP64.
+ * Errors: RK_ERR_INVALID_ARG, RK_ERR_UNSUPPORTED (1D box), RK_ERR_CUDA.
+ */
+rk_status rk_nonlinear_grad_force(rk_handle* h, const double* d, int32_t kind, double c, const double* a, double* fN,
+                                  void* stream);
 rk_status rk_solve_nonlinear(rk_handle* h, const double* r, const double* g, int32_t kind, double c, double* d,
                              double* u, const rk_solve_opts* opts, rk_solve_info* info, void* stream);
 

@@ -574,6 +574,31 @@ PointwiseArgs<T> pointwise_base(const rk_handle* h) {
 template <typename T>
 ZCorrArgs<T> zcorr_args(const rk_handle* h);
 
+// reflected z MERGE of Alg. 2: G_g = sum_{p in g} conv_z(g_p, Tbar_{alpha_z(p)}) from
+// the fields g_p (workspace nX + 2 nY + p) into the z outputs (nX + nY + g)
+template <typename T>
+rk_status reflect_z(rk_handle* h, cudaStream_t s) {
+  const Chain& c = h->chain;
+  const int dbase = c.nX + 2 * c.nY;
+  PassArgs<T> rz = pass_base<T>(h, 2);
+  rz.reflect = 1;
+  rz.n_groups = c.nY;
+  int q = 0;
+  for (int g = 0; g < c.nY; ++g) {
+    rz.out[g] = h->ws<T>(c.nX + c.nY + g);
+    rz.g_io[g] = g;
+    rz.g_begin[g] = q;
+    for (auto& t : c.zterms[g]) {
+      rz.in[t.second] = h->ws<T>(dbase + t.second);
+      rz.term_io[q] = t.second;
+      rz.term_m[q] = t.first;
+      ++q;
+    }
+  }
+  rz.g_begin[c.nY] = q;
+  return run_merge<T>(h, 2, rz, s);
+}
+
 template <typename T>
 rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uint8_t* out_mask, cudaStream_t s,
                const CGFuse<T>* fuse = nullptr) {
@@ -659,24 +684,25 @@ rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uin
     cudaError_t e = launch_pointwise_stiff<T>(pw, s);
     if (e != cudaSuccess) return cuda_fail(e, "pointwise stage");
   }
-  PassArgs<T> rz = pass_base<T>(h, 2);
-  rz.reflect = 1;
-  rz.n_groups = c.nY;
-  q = 0;
-  for (int g = 0; g < c.nY; ++g) {
-    rz.out[g] = h->ws<T>(c.nX + c.nY + g);
-    rz.g_io[g] = g;
-    rz.g_begin[g] = q;
-    for (auto& t : c.zterms[g]) {
-      rz.in[t.second] = h->ws<T>(dbase + t.second);
-      rz.term_io[q] = t.second;
-      rz.term_m[q] = t.first;
-      ++q;
-    }
-  }
-  rz.g_begin[c.nY] = q;
-  RK_TRY(run_merge<T>(h, 2, rz, s));
+  RK_TRY(reflect_z<T>(h, s));
   return chain_reflect_yx<T>(h, f, out_mask, s, fuse);
+}
+
+// The reflected chain of Alg. 2 applied to fields g_p held where the pointwise
+// stage leaves them (3D: workspace field nX + 2 nY + p; 2D: the y-pass output of
+// p): f = out_mask o sum_p conv(g_p, Hbar^a_p).  With g_p = chi V sum_k b^k_p N^k
+// this is B^T N, the gradient-type force of Eq. B.10.
+template <typename T>
+rk_status op_BT(rk_handle* h, T* f, const uint8_t* out_mask, cudaStream_t s) {
+  if (h->dim == 2) return chain_reflect_yx<T>(h, f, out_mask, s, nullptr, h->chain.nX);
+  RK_TRY(reflect_z<T>(h, s));
+  return chain_reflect_yx<T>(h, f, out_mask, s);
+}
+
+// workspace field of g_p for op_BT
+inline int g_field(const rk_handle* h, int p) {
+  const Chain& c = h->chain;
+  return h->dim == 2 ? field_2d(c, p) : c.nX + 2 * c.nY + p;
 }
 
 // Alg. 3: u = chi o sum_p b^0_p o conv(chi o d, H^a_p)
@@ -1588,6 +1614,22 @@ rk_status nonlinear_force(rk_handle* h, const double* d, int kind, double c, dou
   RK_TRY(op_U<double>(h, d, u, s));
   RK_CK(launch_nl_apply(Nu, u, h->chi, kind, c, h->nbox, s));
   return op_UT<double>(h, Nu, fN, h->chiV64, nullptr, s);
+}
+
+// Gradient-type force (Eq. B.5-B.8 in the form of Eq. B.10): N^k = a_k N(u^h) with
+// a fixed direction a, f^N = chi o sum_p conv(chi V sum_k b^k_p N^k, Hbar^a_p) =
+// B^T N -- u^h by Alg. 3, the fields g_p, then the reflected chain of Alg. 2.
+rk_status nonlinear_grad_force(rk_handle* h, const double* d, int kind, double c, const double a[3], double* fN,
+                               cudaStream_t s) {
+  RK_TRY(ensure_transient(h));
+  double* u = h->trans64;
+  double* Nu = h->trans64 + (size_t)1 * h->nbox;
+  RK_TRY(op_U<double>(h, d, u, s));
+  RK_CK(launch_nl_apply(Nu, u, h->chi, kind, c, h->nbox, s));
+  double* g[10];
+  for (int p = 0; p < h->s; ++p) g[p] = h->ws<double>(g_field(h, p));
+  RK_CK(launch_grad_g(g, h->b64, h->chiV64, Nu, a, h->s, h->nbox, s));
+  return op_BT<double>(h, fN, h->chi, s);
 }
 
 // Alg. B.3: K d + f^N(d) = f^r on the free nodes, d = g on Gamma_g, by nonlinear
@@ -2706,6 +2748,22 @@ rk_status rk_nonlinear_force(rk_handle* h, const double* d, int32_t kind, double
   RK_TRY(stage_in(h, 0, d, bytes, s, &sd));
   RK_TRY(stage_out_prepare(h, 1, fN, bytes, &sf));
   RK_TRY(nonlinear_force(h, (const double*)sd.dev, kind, c, (double*)sf.dev, s));
+  RK_TRY(stage_out_finish(sf, s));
+  if (any_host({&sd, &sf})) RK_CK(cudaStreamSynchronize(s));
+  return RK_OK;
+}
+
+rk_status rk_nonlinear_grad_force(rk_handle* h, const double* d, int32_t kind, double c, const double* a,
+                                  double* fN, void* stream) {
+  if (!h || !d || !a || !fN || kind < RK_NL_CUBIC || kind > RK_NL_EXP) return fail(RK_ERR_INVALID_ARG, "bad argument");
+  if (h->dim < 2) return fail(RK_ERR_UNSUPPORTED, "gradient-type force: 2D and 3D boxes");
+  const double av[3] = {a[0], a[1], h->dim == 3 ? a[2] : 0.0};
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->nbox * 8;
+  Staged sd, sf;
+  RK_TRY(stage_in(h, 0, d, bytes, s, &sd));
+  RK_TRY(stage_out_prepare(h, 1, fN, bytes, &sf));
+  RK_TRY(nonlinear_grad_force(h, (const double*)sd.dev, kind, c, av, (double*)sf.dev, s));
   RK_TRY(stage_out_finish(sf, s));
   if (any_host({&sd, &sf})) RK_CK(cudaStreamSynchronize(s));
   return RK_OK;

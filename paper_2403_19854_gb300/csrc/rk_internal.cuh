@@ -168,6 +168,9 @@ cudaError_t launch_u8_to_f64(double* out, const uint8_t* m, long long n, cudaStr
 // nonlinear reaction terms (kind 0: c u^3, 1: c sinh u, 2: c exp u)
 cudaError_t launch_nl_apply(double* Nu, const double* u, const uint8_t* chi, int kind, double c, long long n,
                             cudaStream_t s);
+// g_p = chi V (sum_k a_k b^k_p) N_u for p < s (b = [4][s][n]; the gradient-type force, Eq. B.10)
+cudaError_t launch_grad_g(double* const* g, const double* b, const double* chiV, const double* Nu, const double a[3],
+                          int s, long long n, cudaStream_t st);
 // out2 = {sum_chi V w N(u + alpha w), sum_chi V w^2 N'(u + alpha w)}; partials2 holds 2 x kRedBlocks
 cudaError_t launch_nl_line(const double* u, const double* w, const double* V, const uint8_t* chi, int kind, double c,
                            double alpha, long long n, double* partials2, double* out2, cudaStream_t s);

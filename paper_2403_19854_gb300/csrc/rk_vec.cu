@@ -624,6 +624,28 @@ cudaError_t launch_nl_apply(double* Nu, const double* u, const uint8_t* chi, int
   return cudaGetLastError();
 }
 
+// Fields of the gradient-type force (Eq. B.10): g_p = chi V (sum_k a_k b^k_p) N_u,
+// b = [4][s][n] (b^0, b^x, b^y, b^z), chiV = chi o V, Nu = N(u^h) (zero outside chi)
+__global__ void k_grad_g(DPtrs<double> g, const double* b, const double* chiV, const double* Nu, double a0, double a1,
+                         double a2, int s, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double w = chiV[i] * Nu[i];
+    for (int p = 0; p < s; ++p) {
+      const double bk = a0 * b[(size_t)(s + p) * n + i] + a1 * b[(size_t)(2 * s + p) * n + i] +
+                        a2 * b[(size_t)(3 * s + p) * n + i];
+      g.p[p][i] = w * bk;
+    }
+  }
+}
+cudaError_t launch_grad_g(double* const* g, const double* b, const double* chiV, const double* Nu, const double a[3],
+                          int s, long long n, cudaStream_t st) {
+  DPtrs<double> gp;
+  for (int p = 0; p < 10; ++p) gp.p[p] = p < s ? g[p] : nullptr;
+  count_launch();
+  k_grad_g<<<kRedBlocks, kRedThreads, 0, st>>>(gp, b, chiV, Nu, a[0], a[1], a[2], s, n);
+  return cudaGetLastError();
+}
+
 // Line search sums over chi: out[0] = sum V w N(u + alpha w), out[1] = sum V w^2 N'(u + alpha w)
 // (fixed grid and order: reproducible)
 __global__ void __launch_bounds__(kRedThreads) k_nl_line(const double* u, const double* w, const double* V,

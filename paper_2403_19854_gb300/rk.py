@@ -29,7 +29,7 @@ EXPORTED = ["rk_default_solve_opts", "rk_supported_length", "rk_setup", "rk_sing
             "rk_kernel_launches", "rk_profile_enable", "rk_profile_read", "rk_profile_class_name",
             "rk_solve_vjp", "rk_clone", "rk_solve_batched", "rk_apply_precond", "rk_boundary_rhs",
             "rk_solve_neumann", "rk_apply_M", "rk_lumped_mass", "rk_transient_explicit", "rk_transient_implicit",
-            "rk_nonlinear_force", "rk_solve_nonlinear", "rk_debug_short_waits", "rk_apply_K_noalloc"]
+            "rk_nonlinear_force", "rk_nonlinear_grad_force", "rk_solve_nonlinear", "rk_debug_short_waits", "rk_apply_K_noalloc"]
 NONLINEARITIES = {"cubic": 0, "sinh": 1, "exp": 2}
 PROF_CLASSES = 12
 
@@ -86,6 +86,7 @@ def lib():
     L.rk_boundary_rhs.argtypes = [vp, vp, vp, vp, vp]
     L.rk_apply_M.argtypes = [vp, vp, vp, i32, vp]
     L.rk_nonlinear_force.argtypes = [vp, vp, i32, ctypes.c_double, vp, vp]
+    L.rk_nonlinear_grad_force.argtypes = [vp, vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp, vp]
     L.rk_solve_nonlinear.argtypes = [vp, vp, vp, i32, ctypes.c_double, vp, vp, ctypes.POINTER(SolveOpts),
                                      ctypes.POINTER(SolveInfo), vp]
     L.rk_lumped_mass.argtypes = [vp, vp, vp]
@@ -381,6 +382,18 @@ class Handle:
         po, ko = _ptr(out)
         _check(lib().rk_nonlinear_force(self._h, pd, NONLINEARITIES[kind], float(c), po,
                                         stream if stream is not None else _stream(d)))
+        return out
+
+    def nonlinear_grad_force(self, d, kind, c, a, out=None, stream=None):
+        """Gradient-type force of Eq. B.5-B.8 / B.10: B^T N with N^k = a_k N(u^h),
+        N in NONLINEARITIES times c, a a 3-vector (a[2] unused in 2D)."""
+        if out is None:
+            out = _like(d, RK_F64, self.nbox)
+        av = (ctypes.c_double * 3)(*[float(v) for v in a])
+        pd, kd = _ptr(d)
+        po, ko = _ptr(out)
+        _check(lib().rk_nonlinear_grad_force(self._h, pd, NONLINEARITIES[kind], float(c), av, po,
+                                             stream if stream is not None else _stream(d)))
         return out
 
     def solve_nonlinear(self, r, g, kind, c, d=None, u=None, opts=None, stream=None, raise_on_error=True, **kw):

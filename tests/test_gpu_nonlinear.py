@@ -46,6 +46,35 @@ def test_nonlinear_force(kind, deg, a):
     H.close()
 
 
+GRAD_CASES = [("cube", 16, 2.5, 1), ("cube", 16, 3.0, 2), ("spheres", 32, 2.5, 1), ("plane", 32, 2.5, 2)]
+
+
+@pytest.mark.parametrize("kind", ["cubic", "sinh", "exp"])
+@pytest.mark.parametrize("geom,nb,a,deg", GRAD_CASES)
+def test_gradient_type_force_eq_b10(kind, geom, nb, a, deg):
+    """f^N = B^T N with N^k = a_k N(u^h) (Eq. B.5-B.8 in the form of Eq. B.10),
+    against the oracle's explicit shape-function gradients (Eq. B.6 with direct
+    nodal integration); the oracle's B^T is pinned by gradient reproduction."""
+    if geom == "cube":
+        p = W.cube_problem(nb, a, deg, "sin")
+    elif geom == "spheres":
+        p = W.spheres_problem(n_box=nb, n_spheres=3, a_tilde=a, degree=deg, r_range=(0.2, 0.3), seed=8)
+    else:
+        p = W.plane_problem(nb, a, deg)
+    H = rk.Handle.from_problem(p, device=DEV)
+    o = Oracle(p.n, p.h, a, deg, p.chi)
+    av = [0.7, -1.3, 0.4 if p.n[2] > 1 else 0.0]
+    d = 0.5 * W.random_field(p.nbox, 3) * p.chi
+    u = o.eval_u(d)
+    Nu = 2.0 * N[kind][0](u) * p.chi
+    fo = o.grad_transpose(p.V, np.stack([av[k] * Nu for k in range(3)]))
+    f = np_(H.nonlinear_grad_force(tdev(d), kind, 2.0, av))
+    assert rel(f, fo) < 1e-10, rel(f, fo)
+    assert np.abs(f - fo).max() <= 1e-10 * np.abs(fo).max()
+    assert np.all(f[p.chi == 0] == 0.0)
+    H.close()
+
+
 def _newton_reference(p, o, kind, c):
     o.assemble_K(p.V)
     ptr, col, val = o.K_csr()
