@@ -269,6 +269,26 @@ rk_status rk_transient_implicit(rk_handle* h, const double* f, const double* g, 
  *   used).  u may be NULL.  info: iterations, relative residual, operator
  *   applications.  Errors: RK_ERR_NOT_CONVERGED, RK_ERR_BREAKDOWN (line search).
  */
+/*
+ * rk_solve_penalty -- essential boundary conditions imposed weakly by the penalty
+ * method (Sec. 2.4) instead of Eq. 29: every chi node is free, and
+ *   (K + beta U^T diag(A) U) d = f^r + beta U^T (A o g)
+ * where U is the nodal interpolation of Alg. 3 (u^h at the nodes), A the boundary
+ * quadrature weights (direct nodal quadrature on the boundary nodes, as Eq. A.2;
+ * zero off the boundary) and beta > 0 the penalty parameter.  Solved by CG in FP64
+ * to ||rhs - M d|| <= opts->tol ||rhs|| (opts->max_iter iterations at most; the
+ * precision and mixed options are not used).
+ *   r, g, A: [nbox] inputs (r the source of f^r, g the boundary data);
+ *   d: [nbox] output; u: [nbox] output u^h (NULL: not computed).
+ *   info: iterations, rel_residual, matvec_f64 (applications of the operator).
+ * The solution tends to the one with u^h = g on the boundary nodes as beta grows,
+ * at rate 1/beta; the CG iteration count grows with beta.
+ * Errors: RK_ERR_INVALID_ARG (beta <= 0, NULL arrays, non-finite right-hand
+ * side), RK_ERR_NOT_CONVERGED, RK_ERR_BREAKDOWN, RK_ERR_CUDA.
+ */
+rk_status rk_solve_penalty(rk_handle* h, const double* r, const double* g, const double* A, double beta, double* d,
+                           double* u, const rk_solve_opts* opts, rk_solve_info* info, void* stream);
+
 typedef enum rk_nonlinearity { RK_NL_CUBIC = 0, RK_NL_SINH = 1, RK_NL_EXP = 2 } rk_nonlinearity;
 rk_status rk_nonlinear_force(rk_handle* h, const double* d, int32_t kind, double c, double* fN, void* stream);
 /*

@@ -1632,6 +1632,79 @@ rk_status nonlinear_grad_force(rk_handle* h, const double* d, int kind, double c
   return op_BT<double>(h, fN, h->chi, s);
 }
 
+// Essential boundary conditions imposed weakly by the penalty method (Sec. 2.4):
+// the weak form gains beta * int_{Gamma_g} w (u - g) dGamma, with direct nodal
+// quadrature on the boundary nodes (weights A, as Eq. A.2) and w, u the RK
+// approximations at those nodes (u^h of Alg. 3).  Every chi node is free:
+//   (K + beta U^T diag(A) U) d = f^r + beta U^T (A o g),
+// with U the nodal interpolation of Alg. 3 and U^T its transpose (the chain of
+// Alg. 4 with weights A).  The operator is symmetric positive definite for
+// beta > 0 (K is positive semi-definite with the constants in its null space, and
+// U^T diag(A) U is positive on them), so plain CG in FP64 solves it.
+rk_status solve_penalty(rk_handle* h, const double* r, const double* g, const double* A, double beta, double* d,
+                        const rk_solve_opts& o, rk_solve_info* info, cudaStream_t s) {
+  RK_TRY(ensure_solver(h));
+  const long long n = h->nbox;
+  double* x = h->v64(0);
+  double* res = h->v64(1);
+  double* p = h->v64(2);
+  double* Ap = h->v64(3);
+  double* b = h->v64(4);
+  double* t = h->v64(5);
+  double* u = h->v64(6);
+  // M v = chi o K (chi o v) + beta U^T (A o U v)
+  auto apply = [&](const double* v, double* out) -> rk_status {
+    RK_TRY(op_K<double>(h, v, out, h->chi, h->chi, s));
+    RK_TRY(op_U<double>(h, v, u, s));
+    RK_TRY(op_UT<double>(h, u, t, A, nullptr, s));
+    RK_CK(launch_axpby(out, beta, t, 1.0, n, s));
+    info->matvec_f64++;
+    return RK_OK;
+  };
+  RK_TRY(op_UT<double>(h, r, b, h->chiV64, nullptr, s));  // f^r (Alg. 4)
+  RK_TRY(op_UT<double>(h, g, t, A, nullptr, s));          // U^T (A o g)
+  RK_CK(launch_axpby(b, beta, t, 1.0, n, s));
+  double bn;
+  RK_TRY(norm2(h, b, &bn, s));
+  info->f_norm = bn;
+  if (!std::isfinite(bn)) return fail(RK_ERR_INVALID_ARG, "right-hand side is not finite");
+  RK_CK(launch_fill<double>(x, 0.0, n, s));
+  RK_CK(launch_copy<double>(res, b, n, s));
+  RK_CK(launch_copy<double>(p, b, n, s));
+  double rr;
+  RK_CK(launch_dot<double, double>(res, res, n, h->partials, h->dscal, s));
+  RK_TRY(read_scalar(h, h->dscal, &rr, s));
+  const double target = o.tol * bn;
+  int it = 0;
+  while (std::sqrt(rr) > target && it < o.max_iter) {
+    RK_TRY(apply(p, Ap));
+    double pAp;
+    RK_CK(launch_dot<double, double>(p, Ap, n, h->partials, h->dscal, s));
+    RK_TRY(read_scalar(h, h->dscal, &pAp, s));
+    if (!(pAp > 0.0) || !std::isfinite(pAp)) return fail(RK_ERR_BREAKDOWN, "penalty CG: p.Ap <= 0");
+    const double alpha = rr / pAp;
+    RK_CK(launch_axpby(x, alpha, p, 1.0, n, s));
+    RK_CK(launch_axpby(res, -alpha, Ap, 1.0, n, s));
+    double rr_new;
+    RK_CK(launch_dot<double, double>(res, res, n, h->partials, h->dscal, s));
+    RK_TRY(read_scalar(h, h->dscal, &rr_new, s));
+    RK_CK(launch_axpby(p, 1.0, res, rr_new / rr, n, s));
+    rr = rr_new;
+    ++it;
+  }
+  // the true residual of the final iterate
+  RK_TRY(apply(x, Ap));
+  RK_CK(launch_sub(res, b, Ap, n, s));
+  double rn;
+  RK_TRY(norm2(h, res, &rn, s));
+  info->iterations = it;
+  info->fp64_iterations = it;
+  info->rel_residual = bn > 0.0 ? rn / bn : 0.0;
+  RK_CK(launch_copy<double>(d, x, n, s));
+  if (!(rn <= target)) return fail(RK_ERR_NOT_CONVERGED, "penalty CG: iteration cap reached");
+  return RK_OK;
+}
+
 // Alg. B.3: K d + f^N(d) = f^r on the free nodes, d = g on Gamma_g, by nonlinear
 // CG (Polak-Ribiere+) on the convex energy E = 1/2 d.K d + sum_S V_S F(u_S) - d.f^r
 // (F' = N, nondecreasing).  The line search along p is Newton's method on
@@ -2751,6 +2824,44 @@ rk_status rk_nonlinear_force(rk_handle* h, const double* d, int32_t kind, double
   RK_TRY(stage_out_finish(sf, s));
   if (any_host({&sd, &sf})) RK_CK(cudaStreamSynchronize(s));
   return RK_OK;
+}
+
+rk_status rk_solve_penalty(rk_handle* h, const double* r, const double* g, const double* A, double beta, double* d,
+                           double* u, const rk_solve_opts* opts, rk_solve_info* info, void* stream) {
+  if (!h || !r || !g || !A || !d || !(beta > 0.0) || !std::isfinite(beta)) return fail(RK_ERR_INVALID_ARG, "bad argument");
+  rk_solve_opts o;
+  if (opts)
+    o = *opts;
+  else
+    fill_defaults(&o);
+  RK_TRY(check_opts(o));
+  rk_solve_info inf;
+  memset(&inf, 0, sizeof(inf));
+  cudaStream_t s = (cudaStream_t)stream;
+  auto t0 = std::chrono::steady_clock::now();
+  const size_t bytes = (size_t)h->nbox * 8;
+  RK_TRY(ensure_solver(h));
+  Staged sr, sg, sa, sd, su;
+  RK_TRY(stage_in(h, 0, r, bytes, s, &sr));
+  RK_TRY(stage_in(h, 1, g, bytes, s, &sg));
+  RK_TRY(stage_in(h, 2, A, bytes, s, &sa));
+  RK_TRY(stage_out_prepare(h, 3, d, bytes, &sd));
+  rk_status st = solve_penalty(h, (const double*)sr.dev, (const double*)sg.dev, (const double*)sa.dev, beta,
+                               (double*)sd.dev, o, &inf, s);
+  if (st == RK_OK || st == RK_ERR_NOT_CONVERGED) {
+    RK_TRY(stage_out_finish(sd, s));
+    if (u) {
+      RK_TRY(stage_out_prepare(h, 4, u, bytes, &su));
+      RK_TRY(op_U<double>(h, (const double*)sd.dev, (double*)su.dev, s));
+      RK_TRY(stage_out_finish(su, s));
+    }
+  }
+  RK_CK(cudaStreamSynchronize(s));
+  RK_TRY(check_device_flag(h));
+  inf.status = st;
+  inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  return st;
 }
 
 rk_status rk_nonlinear_grad_force(rk_handle* h, const double* d, int32_t kind, double c, const double* a,

@@ -29,7 +29,7 @@ EXPORTED = ["rk_default_solve_opts", "rk_supported_length", "rk_setup", "rk_sing
             "rk_kernel_launches", "rk_profile_enable", "rk_profile_read", "rk_profile_class_name",
             "rk_solve_vjp", "rk_clone", "rk_solve_batched", "rk_apply_precond", "rk_boundary_rhs",
             "rk_solve_neumann", "rk_apply_M", "rk_lumped_mass", "rk_transient_explicit", "rk_transient_implicit",
-            "rk_nonlinear_force", "rk_nonlinear_grad_force", "rk_solve_nonlinear", "rk_debug_short_waits", "rk_apply_K_noalloc"]
+            "rk_nonlinear_force", "rk_nonlinear_grad_force", "rk_solve_penalty", "rk_solve_nonlinear", "rk_debug_short_waits", "rk_apply_K_noalloc"]
 NONLINEARITIES = {"cubic": 0, "sinh": 1, "exp": 2}
 PROF_CLASSES = 12
 
@@ -86,6 +86,8 @@ def lib():
     L.rk_boundary_rhs.argtypes = [vp, vp, vp, vp, vp]
     L.rk_apply_M.argtypes = [vp, vp, vp, i32, vp]
     L.rk_nonlinear_force.argtypes = [vp, vp, i32, ctypes.c_double, vp, vp]
+    L.rk_solve_penalty.argtypes = [vp, vp, vp, vp, ctypes.c_double, vp, vp, ctypes.POINTER(SolveOpts),
+                                   ctypes.POINTER(SolveInfo), vp]
     L.rk_nonlinear_grad_force.argtypes = [vp, vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp, vp]
     L.rk_solve_nonlinear.argtypes = [vp, vp, vp, i32, ctypes.c_double, vp, vp, ctypes.POINTER(SolveOpts),
                                      ctypes.POINTER(SolveInfo), vp]
@@ -411,6 +413,27 @@ class Handle:
         pu, ku = _ptr(u)
         st = lib().rk_solve_nonlinear(self._h, pr, pg, NONLINEARITIES[kind], float(c), pd, pu, ctypes.byref(opts),
                                       ctypes.byref(info), stream if stream is not None else _stream(r))
+        if raise_on_error:
+            _check(st)
+        return d, u, info.as_dict()
+
+    def solve_penalty(self, r, g, A, beta, d=None, u=None, opts=None, stream=None, raise_on_error=True, **kw):
+        """Essential conditions by the penalty method (Sec. 2.4): (K + beta U^T diag(A) U) d =
+        f^r + beta U^T (A g) over every chi node, FP64 CG.  Returns (d, u, info dict)."""
+        if opts is None:
+            opts = default_opts(**kw)
+        if d is None:
+            d = _like(r, RK_F64, self.nbox)
+        if u is None:
+            u = _like(r, RK_F64, self.nbox)
+        info = SolveInfo()
+        pr, kr = _ptr(r)
+        pg, kg = _ptr(g)
+        pa, ka = _ptr(A)
+        pd, kd = _ptr(d)
+        pu, ku = _ptr(u)
+        st = lib().rk_solve_penalty(self._h, pr, pg, pa, float(beta), pd, pu, ctypes.byref(opts), ctypes.byref(info),
+                                    stream if stream is not None else _stream(r))
         if raise_on_error:
             _check(st)
         return d, u, info.as_dict()

@@ -79,6 +79,27 @@ def _face_flags(n_box, n_omega):
     return inside, face
 
 
+def cube_surface_weights(p):
+    """Boundary quadrature weights A of a cube_problem domain (the boundary
+    integrals of Sec. 2.4 and Appendix A with direct nodal quadrature): a node on a
+    face normal to axis k gets the 2D trapezoidal share of that face, h^2 halved
+    once per in-face axis on which it lies on the face's edge; a node on several
+    faces (an edge or a corner of the cube) sums its shares.  Zero off the faces."""
+    nb = p.n[0]
+    h = p.h[0]
+    chi3 = p.chi.reshape(p.n[2], p.n[1], p.n[0])
+    n_om = int(chi3[0, 0, :].sum())
+    inside, face = _face_flags(nb, n_om)
+    ins3 = inside[None, None, :] & inside[None, :, None] & inside[:, None, None]
+    fk = [face[None, None, :], face[None, :, None], face[:, None, None]]  # x, y, z
+    A = np.zeros((nb, nb, nb))
+    for k in range(3):
+        o1, o2 = [fk[m] for m in range(3) if m != k]
+        w = h * h * 0.5 ** (o1.astype(np.int32) + o2.astype(np.int32))
+        A = A + np.where(ins3 & fk[k], w, 0.0)
+    return A.reshape(-1)
+
+
 def cube_problem(n_box, a_tilde, degree=1, kind="sin", lo=0.0, hi=1.0):
     """Cube domain [lo, hi]^3 meshed by n_omega = n_box - floor(a_tilde) nodes per
     axis (h = (hi - lo)/(n_omega - 1)), embedded in an n_box^3 periodic box.

@@ -83,3 +83,46 @@ def test_mixed_boundary_solve(prec):
     d0, _, _ = H.solve(tdev(p.r), tdev(p.g), precision=prec, tol=1e-13)
     assert rel(np_(d0), do) > 1e-3
     H.close()
+
+
+def _dense_tables(p, o):
+    import scipy.sparse as sp
+    o.assemble_K(p.V)
+    ptr, col, val = o.K_csr()
+    nodes = np.flatnonzero(p.chi)
+    nn = len(nodes)
+    K = sp.csr_matrix((val, col, ptr), shape=(nn, nn)).toarray()
+    nbr, psi, _ = o.shape_tables()
+    rows, cols = np.nonzero(nbr >= 0)
+    U = sp.csr_matrix((psi[rows, cols], (rows, nbr[rows, cols])), shape=(nn, nn)).toarray()
+    return nodes, K, U
+
+
+@pytest.mark.parametrize("a,deg", [(2.5, 1), (3.0, 2)])
+def test_penalty_solve_matches_oracle(a, deg):
+    """Essential conditions by the penalty method (Sec. 2.4): the GPU solve of
+    (K + beta U^T diag(A) U) d = f^r + beta U^T (A g) against the dense solve of the
+    same system built from the oracle's assembled K and shape functions U, with the
+    cube's face weights A and beta = 100 max|K| / max A; d and u^h to 1e-9."""
+    p = W.cube_problem(16, a, deg, "zero")
+    o = Oracle(p.n, p.h, a, deg, p.chi)
+    nodes, K, U = _dense_tables(p, o)
+    A = W.cube_surface_weights(p)
+    rng = np.random.default_rng(29)
+    r = W.random_field(p.nbox, 11) * p.chi
+    g = np.where(A > 0, rng.standard_normal(p.nbox), 0.0)
+    beta = 100.0 * np.abs(K).max() / A.max()
+    An = A[nodes]
+    M = K + beta * (U.T * An) @ U
+    rhs = o.rhs(p.V, r)[nodes] + beta * U.T @ (An * g[nodes])
+    do = np.zeros(p.nbox)
+    do[nodes] = np.linalg.solve(M, rhs)
+    uo = np.zeros(p.nbox)
+    uo[nodes] = U @ do[nodes]
+    H = rk.Handle.from_problem(p, device=DEV)
+    d, u, info = H.solve_penalty(tdev(r), tdev(g), tdev(A), beta, tol=1e-13, max_iter=20000)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-13
+    assert rel(np_(d), do) < 1e-9, rel(np_(d), do)
+    assert rel(np_(u), uo) < 1e-9
+    assert np.all(np_(d)[p.chi == 0] == 0.0)
+    H.close()

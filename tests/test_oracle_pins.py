@@ -293,6 +293,54 @@ def test_rhs_moments():
         assert lhs == pytest.approx(rhs, rel=1e-12, abs=1e-15)
 
 
+def _dense_tables(p, o):
+    """(nodes, K, U) over the chi nodes in node order: the oracle's assembled K
+    (Eq. 26, DNI) and U[S, J] = Psi_J(x_S) (Eq. 2) from its shape tables."""
+    import scipy.sparse as sp
+    o.assemble_K(p.V)
+    ptr, col, val = o.K_csr()
+    nodes = np.flatnonzero(p.chi)
+    nn = len(nodes)
+    K = sp.csr_matrix((val, col, ptr), shape=(nn, nn)).toarray()
+    nbr, psi, _ = o.shape_tables()
+    rows, cols = np.nonzero(nbr >= 0)
+    U = sp.csr_matrix((psi[rows, cols], (rows, nbr[rows, cols])), shape=(nn, nn)).toarray()
+    return nodes, K, U
+
+
+def test_penalty_solution_tends_to_the_constrained_one():
+    """Essential conditions by the penalty method (Sec. 2.4): the solution of
+    (K + beta U^T diag(A) U) d = f^r + beta U^T (A g) tends, as beta grows, to the
+    Lagrange-multiplier solution of min 1/2 d.K d - d.f^r subject to u^h = g on the
+    boundary nodes, with an error O(1/beta).  Built densely from the oracle's K and
+    U on a 10^3-node cube (surface weights A of its faces)."""
+    p = W.cube_problem(12, 2.5, 1, "zero")
+    o = Oracle(p.n, p.h, 2.5, 1, p.chi)
+    nodes, K, U = _dense_tables(p, o)
+    A = W.cube_surface_weights(p)[nodes]
+    gam = A > 0
+    assert gam.sum() == 10 ** 3 - 8 ** 3
+    rng = np.random.default_rng(23)
+    r = W.random_field(p.nbox, 7) * p.chi
+    f = o.rhs(p.V, r)[nodes]
+    g = np.where(gam, rng.standard_normal(len(nodes)), 0.0)
+    C = U[gam]
+    nc = C.shape[0]
+    kkt = np.block([[K, C.T], [C, np.zeros((nc, nc))]])
+    d_kkt = np.linalg.solve(kkt, np.concatenate([f, g[gam]]))[: len(nodes)]
+    assert np.abs(C @ d_kkt - g[gam]).max() < 1e-9
+    scale = np.abs(K).max() / A.max()
+    errs = []
+    for bt in (1e2, 1e3, 1e4, 1e5):
+        beta = bt * scale
+        M = K + beta * (U.T * A) @ U
+        d = np.linalg.solve(M, f + beta * U.T @ (A * g))
+        errs.append(np.linalg.norm(d - d_kkt) / np.linalg.norm(d_kkt))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(5.0 < q < 20.0 for q in ratios), (errs, ratios)
+    assert errs[-1] < 1e-3
+
+
 @pytest.mark.parametrize("deg,a", [(1, 2.5), (2, 3.0)])
 def test_grad_force_moments(deg, a):
     """The gradient-type nonlinear force of Eq. B.6-B.8, f_J = sum_S V_S sum_k
