@@ -298,8 +298,8 @@ rk_status rk_nonlinear_force(rk_handle* h, const double* d, int32_t kind, double
  * (sum over p), evaluated as u^h (Alg. 3), the fields g_p = chi V sum_k a_k b^k_p N,
  * and the reflected passes of Alg. 2.  N is the pointwise nonlinearity kind with
  * coefficient c (as rk_nonlinear_force); a[3] (host) is the fixed direction of the
- * vector nonlinearity (a[2] is ignored on a 2D box).  d, fN: [nbox], FP64.
- * Errors: RK_ERR_INVALID_ARG, RK_ERR_UNSUPPORTED (1D box), RK_ERR_CUDA.
+ * vector nonlinearity (a[2] is ignored on a 2D box, a[1] and a[2] on a 1D box).
+ * d, fN: [nbox], FP64.  Errors: RK_ERR_INVALID_ARG, RK_ERR_CUDA.
  */
 rk_status rk_nonlinear_grad_force(rk_handle* h, const double* d, int32_t kind, double c, const double* a, double* fN,
                                   void* stream);

@@ -68,14 +68,15 @@ bool is_device_ptr(const void* p) {
 
 // Monomial exponents of the basis (Eq. 4 in 3D), graded order; in 2D (dim = 2) the
 // monomials free of z, in the same order ([1, x, y] / [1, x, y, x^2, xy, y^2]: the
-// paper states the method in 2D).  Returns s.
+// paper states the method in 2D), in 1D those free of y and z ([1, x] / [1, x, x^2],
+// Sec. 6.1.1).  Returns s.
 int basis_exponents(int degree, int dim, int alpha[][3]) {
   static const int e[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
                                {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
   const int n3 = degree == 1 ? 4 : 10;
   int s = 0;
   for (int p = 0; p < n3; ++p) {
-    if (dim < 3 && e[p][2] != 0) continue;
+    if ((dim < 3 && e[p][2] != 0) || (dim < 2 && e[p][1] != 0)) continue;
     for (int k = 0; k < 3; ++k) alpha[s][k] = e[p][k];
     ++s;
   }
@@ -116,7 +117,7 @@ struct Chain {
 // --------------------------------------------------------------------- handle
 struct rk_handle {
   int n[3];
-  int dim = 3;  // 2 when n[2] == 1: no z axis (no z kernel factor, monomial or gradient)
+  int dim = 3;  // 2 when n[2] == 1: no z axis (no z kernel factor, monomial or gradient); 1 when n[1] == n[2] == 1
   double h[3];
   double a_tilde;
   int degree, s;
@@ -446,6 +447,7 @@ rk_status chain_forward_xy(rk_handle* h, const T* d, const uint8_t* in_mask, cud
   }
   ax.g_begin[1] = c.nX;
   RK_TRY(run_split<T>(h, 0, ax, s));
+  if (h->dim == 1) return RK_OK;  // 1D: the x outputs are the D_p
   PassArgs<T> ay = pass_base<T>(h, 1);
   ay.n_groups = c.nX;
   int q = 0;
@@ -490,7 +492,7 @@ rk_status chain_reflect_yx(rk_handle* h, T* f, const uint8_t* out_mask, cudaStre
       }
   }
   ay.g_begin[c.nX] = q;
-  RK_TRY(run_merge<T>(h, 1, ay, s));
+  if (h->dim > 1) RK_TRY(run_merge<T>(h, 1, ay, s));  // 1D: the g_p already sit in the x fields
   PassArgs<T> ax = pass_base<T>(h, 0);
   ax.reflect = 1;
   ax.out_mask = out_mask;
@@ -557,6 +559,11 @@ inline int field_2d(const Chain& c, int p) {
     if (c.zterms[g][0].second == p) return c.nX + g;
   return -1;
 }
+// Workspace field of D_p / g_p on a box without a z axis: the y-pass output of p
+// in 2D, the x-pass output of p (m = alpha_x(p)) in 1D.
+inline int field_low(const rk_handle* h, int p) {
+  return h->dim == 1 ? h->chain.alpha[p][0] : field_2d(h->chain, p);
+}
 
 template <typename T>
 PointwiseArgs<T> pointwise_base(const rk_handle* h) {
@@ -604,11 +611,11 @@ rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uin
                const CGFuse<T>* fuse = nullptr) {
   const Chain& c = h->chain;
   RK_TRY(chain_forward_xy<T>(h, d, in_mask, s, fuse));
-  if (h->dim == 2) {
-    // no z axis: the y outputs are the D_p; the pointwise stage in place, then the
-    // reflected y and x passes read the g_p from the same fields
+  if (h->dim < 3) {
+    // no z axis: the y outputs (2D) or x outputs (1D) are the D_p; the pointwise
+    // stage in place, then the reflected passes read the g_p from the same fields
     PointwiseArgs<T> pw = pointwise_base<T>(h);
-    for (int p = 0; p < h->s; ++p) pw.D[p] = h->ws<T>(field_2d(c, p));
+    for (int p = 0; p < h->s; ++p) pw.D[p] = h->ws<T>(field_low(h, p));
     {
       ProfScope ps(h, prof_cls<T>(RK_PROF_Z_STIFF), s);
       cudaError_t e = launch_pointwise_stiff<T>(pw, s);
@@ -694,7 +701,7 @@ rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uin
 // this is B^T N, the gradient-type force of Eq. B.10.
 template <typename T>
 rk_status op_BT(rk_handle* h, T* f, const uint8_t* out_mask, cudaStream_t s) {
-  if (h->dim == 2) return chain_reflect_yx<T>(h, f, out_mask, s, nullptr, h->chain.nX);
+  if (h->dim < 3) return chain_reflect_yx<T>(h, f, out_mask, s, nullptr, h->chain.nX);
   RK_TRY(reflect_z<T>(h, s));
   return chain_reflect_yx<T>(h, f, out_mask, s);
 }
@@ -702,16 +709,16 @@ rk_status op_BT(rk_handle* h, T* f, const uint8_t* out_mask, cudaStream_t s) {
 // workspace field of g_p for op_BT
 inline int g_field(const rk_handle* h, int p) {
   const Chain& c = h->chain;
-  return h->dim == 2 ? field_2d(c, p) : c.nX + 2 * c.nY + p;
+  return h->dim < 3 ? field_low(h, p) : c.nX + 2 * c.nY + p;
 }
 
 // Alg. 3: u = chi o sum_p b^0_p o conv(chi o d, H^a_p)
 template <typename T>
 rk_status op_U(rk_handle* h, const T* d, T* u, cudaStream_t s) {
   RK_TRY(chain_forward_xy<T>(h, d, h->chi, s));
-  if (h->dim == 2) {
+  if (h->dim < 3) {
     T* D[10];
-    for (int p = 0; p < h->s; ++p) D[p] = h->ws<T>(field_2d(h->chain, p));
+    for (int p = 0; p < h->s; ++p) D[p] = h->ws<T>(field_low(h, p));
     ProfScope ps(h, prof_cls<T>(RK_PROF_Z_EVAL_U), s);
     cudaError_t e = launch_eval_u_fields<T>(u, D, bfields<T>(h), h->s, h->chi, h->nbox, s);
     return e == cudaSuccess ? RK_OK : cuda_fail(e, "u^h");
@@ -727,9 +734,9 @@ rk_status op_U(rk_handle* h, const T* d, T* u, cudaStream_t s) {
 // w = chi o sum_p conv(weight o b^0_p o y, Hbar^a_p)
 template <typename T>
 rk_status op_UT(rk_handle* h, const T* y, T* w, const T* wfield, const uint8_t* wmask, cudaStream_t s) {
-  if (h->dim == 2) {
+  if (h->dim < 3) {
     T* D[10];
-    for (int p = 0; p < h->s; ++p) D[p] = h->ws<T>(field_2d(h->chain, p));
+    for (int p = 0; p < h->s; ++p) D[p] = h->ws<T>(field_low(h, p));
     {
       ProfScope ps(h, prof_cls<T>(RK_PROF_Z_TRANSPOSE_U), s);
       cudaError_t e = launch_transpose_u_fields<T>(D, y, bfields<T>(h), h->s, wfield, wmask, h->nbox, s);
@@ -2230,16 +2237,19 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
   if (!grid || !chi || !V) return fail(RK_ERR_INVALID_ARG, "grid, chi and V are required");
   if (degree != 1 && degree != 2) return fail(RK_ERR_INVALID_ARG, "degree must be 1 or 2");
   if (!(a_tilde > 0.5 && a_tilde < 16.0)) return fail(RK_ERR_INVALID_ARG, "a_tilde out of range");
-  const int dim = grid->n[2] == 1 ? 2 : 3;  // a box one node thick in z is two-dimensional
-  if (grid->n[1] == 1) return fail(RK_ERR_UNSUPPORTED, "one-dimensional grids are not built");
+  // a box one node thick in z is two-dimensional, one node thick in y and z one-dimensional
+  const int dim = grid->n[2] == 1 ? (grid->n[1] == 1 ? 1 : 2) : 3;
+  if (grid->n[2] > 1 && grid->n[1] == 1) return fail(RK_ERR_INVALID_ARG, "bad grid: n[1] == 1 < n[2]");
   for (int k = 0; k < 3; ++k) {
     if ((k < dim && grid->n[k] < 2) || grid->n[k] < 1 || !(grid->h[k] > 0.0))
       return fail(RK_ERR_INVALID_ARG, "bad grid");
     if (k < dim && !supported_length(grid->n[k]))
       return fail(RK_ERR_UNSUPPORTED, "box side " + std::to_string(grid->n[k]) + " not built");
   }
-  if (grid->n[0] % 2 != 0 || ((long long)grid->n[1] * grid->n[2]) % 2 != 0)
+  if (grid->n[0] % 2 != 0 || (dim > 1 && ((long long)grid->n[1] * grid->n[2]) % 2 != 0))
     return fail(RK_ERR_UNSUPPORTED, "n[0] and n[1]*n[2] must be even");
+  if (dim == 1 && grid->n[0] % 4 != 0)  // the pointwise stage reads 16-byte vectors of nodes
+    return fail(RK_ERR_UNSUPPORTED, "a 1D box needs n[0] a multiple of 4");
   cudaStream_t s = (cudaStream_t)stream;
   rk_handle* h = new rk_handle();
   auto bail = [&](rk_status st) {
@@ -2257,9 +2267,9 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
   cudaGetDevice(&h->device);
   h->chain.build(degree, dim);
   h->s = h->chain.s;
-  if (dim == 2)
+  if (dim < 3)
     for (int p = 0; p < h->s; ++p)
-      if (field_2d(h->chain, p) < 0) return bail(fail(RK_ERR_INVALID_ARG, "2D basis without a y-pass field"));
+      if (field_low(h, p) < 0) return bail(fail(RK_ERR_INVALID_ARG, "basis without a field of its own"));
   int reach = 0;
   while (kernel_profile((double)(reach + 1) / a_tilde) > 0.0) ++reach;
   h->reach = reach;
@@ -2320,7 +2330,7 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
   std::vector<std::pair<int, int>> ylist;      // (gx, gy)
   std::vector<std::array<int, 3>> zlist;       // (gx, gy, gz)
   for (int gx = 0; gx <= D2; ++gx)
-    for (int gy = 0; gx + gy <= D2; ++gy) ylist.push_back({gx, gy});
+    for (int gy = 0; gx + gy <= D2 && (dim > 1 || gy == 0); ++gy) ylist.push_back({gx, gy});
   std::vector<int> zbegin;
   for (auto& yg : ylist) {
     zbegin.push_back((int)zlist.size());
@@ -2362,7 +2372,7 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
         }
     }
     ay.g_begin[nXm] = q;
-    RK_TRY(run_split<double>(h, 1, ay, s));
+    if (dim > 1) RK_TRY(run_split<double>(h, 1, ay, s));
     PassArgs<double> az = pass_base<double>(h, 2);
     az.n_groups = nYm;
     q = 0;
@@ -2383,7 +2393,8 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
     // per-node M^{-1} -> b (Eq. 83-85)
     MomentArgs ma;
     memset(&ma, 0, sizeof(ma));
-    ma.mom = dim == 3 ? mf(1 + nXm + nYm) : mf(1 + nXm);
+    // 3D: the z outputs; 2D: the y outputs; 1D: the x outputs (zlist = (g_x, 0, 0) in g_x order)
+    ma.mom = dim == 3 ? mf(1 + nXm + nYm) : (dim == 2 ? mf(1 + nXm) : mf(1));
     ma.n_mom = nZm;
     ma.s = h->s;
     ma.dim = dim;
@@ -2867,8 +2878,7 @@ rk_status rk_solve_penalty(rk_handle* h, const double* r, const double* g, const
 rk_status rk_nonlinear_grad_force(rk_handle* h, const double* d, int32_t kind, double c, const double* a,
                                   double* fN, void* stream) {
   if (!h || !d || !a || !fN || kind < RK_NL_CUBIC || kind > RK_NL_EXP) return fail(RK_ERR_INVALID_ARG, "bad argument");
-  if (h->dim < 2) return fail(RK_ERR_UNSUPPORTED, "gradient-type force: 2D and 3D boxes");
-  const double av[3] = {a[0], a[1], h->dim == 3 ? a[2] : 0.0};
+  const double av[3] = {a[0], h->dim > 1 ? a[1] : 0.0, h->dim == 3 ? a[2] : 0.0};
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)h->nbox * 8;
   Staged sd, sf;

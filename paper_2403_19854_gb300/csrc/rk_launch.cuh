@@ -104,7 +104,7 @@ cudaError_t split_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMa
   if (axis == 0) {
     constexpr int LX = Cfg<T>::XTHREADS / LineShape<N>::P;
     using X = XPass<T, N, LX>;
-    const long long npairs = ((long long)a.ny * a.nz) / 2;
+    const long long npairs = ((long long)a.ny * a.nz + 1) / 2;  // an odd last row pairs with zeros
     const unsigned nb = (unsigned)((npairs + LX - 1) / LX);
     PassArgs<T> b = a;
     if (x_bulk_setup<T, N, LX>(b)) {
@@ -133,7 +133,7 @@ cudaError_t merge_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMa
   if (axis == 0) {
     constexpr int LX = Cfg<T>::XTHREADS / LineShape<N>::P;
     using X = XPass<T, N, LX>;
-    const long long npairs = ((long long)a.ny * a.nz) / 2;
+    const long long npairs = ((long long)a.ny * a.nz + 1) / 2;  // an odd last row pairs with zeros
     const unsigned nb = (unsigned)((npairs + LX - 1) / LX);
     auto k = k_x_merge<T, N, LX>;
     cudaError_t e = set_smem(k, X::SMEM);

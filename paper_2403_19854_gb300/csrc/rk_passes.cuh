@@ -460,8 +460,12 @@ RK_DEV void stage_mask_rows(uint8_t* dst, const uint8_t* m, long long first_row,
   const long long nbytes = (long long)2 * LX * N;
   const long long avail = nrows_total * N - b0;
   const long long lim = nbytes < avail ? nbytes : avail;
-  for (long long c = (long long)threadIdx.x * 16; c < lim; c += (long long)blockDim.x * 16)
-    *reinterpret_cast<uint4*>(dst + c) = RK_LDG(reinterpret_cast<const uint4*>(m + b0 + c));
+  for (long long c = (long long)threadIdx.x * 16; c < lim; c += (long long)blockDim.x * 16) {
+    if (c + 16 <= lim)
+      *reinterpret_cast<uint4*>(dst + c) = RK_LDG(reinterpret_cast<const uint4*>(m + b0 + c));
+    else  // the end of the array inside a 16-byte unit (a single row, 1D)
+      for (long long b = c; b < lim; ++b) dst[b] = RK_LDG(m + b0 + b);
+  }
   RK_SYNC();
 }
 
@@ -536,8 +540,10 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
   __shared__ uint64_t bar;
   const int t = threadIdx.x % X::P, l = threadIdx.x / X::P;
   const long long q = (long long)blockIdx.x * LX + l;  // row pair
-  const long long npairs = ((long long)a.ny * a.nz) / 2;
+  const long long nrows_all = (long long)a.ny * a.nz;
+  const long long npairs = (nrows_all + 1) / 2;        // an odd last row pairs with a row of zeros
   const bool ok = q < npairs;
+  const bool ok1 = 2 * q + 1 < nrows_all;
   const long long r0 = 2 * q * a.nx, r1 = r0 + a.nx;
   typename X::B buf{sm + (size_t)l * X::B::SIZE};
   cpx<T> v[X::R], w[X::R];
@@ -565,13 +571,13 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
         if (ok) {
           if (bulk) {
             p0 = ra[xp] + be * tileB[(2 * l) * X::PITCH + xp];
-            p1 = rb[xp] + be * tileB[(2 * l + 1) * X::PITCH + xp];
+            if (ok1) p1 = rb[xp] + be * tileB[(2 * l + 1) * X::PITCH + xp];
           } else {
             p0 = a.cg_r[r0 + xp] + be * a.cg_p[r0 + xp];
-            p1 = a.cg_r[r1 + xp] + be * a.cg_p[r1 + xp];
+            if (ok1) p1 = a.cg_r[r1 + xp] + be * a.cg_p[r1 + xp];
           }
           a.cg_p[r0 + xp] = p0;
-          a.cg_p[r1 + xp] = p1;
+          if (ok1) a.cg_p[r1 + xp] = p1;
         }
         v[r] = cmk(p0, p1);
       }
@@ -582,16 +588,17 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
       for (int r = 0; r < X::R; ++r) {
         const int xp = F::nat_pos(t, r);
         const T x0 = ok ? (bulk ? ra[xp] : RK_LDG(in + r0 + xp)) : (T)0;
-        const T x1 = ok ? (bulk ? rb[xp] : RK_LDG(in + r1 + xp)) : (T)0;
-        v[r] = cmk(x0 * (T)msk[(2 * l) * N + xp], x1 * (T)msk[(2 * l + 1) * N + xp]);
+        const T x1 = ok1 ? (bulk ? rb[xp] : RK_LDG(in + r1 + xp)) : (T)0;
+        v[r] = cmk(x0 * (T)msk[(2 * l) * N + xp], ok1 ? x1 * (T)msk[(2 * l + 1) * N + xp] : (T)0);
       }
     } else {
 #pragma unroll
       for (int r = 0; r < X::R; ++r) {
         const int xp = F::nat_pos(t, r);
         const T x0 = ok ? (bulk ? ra[xp] : RK_LDG(in + r0 + xp)) : (T)0;
-        const T x1 = ok ? (bulk ? rb[xp] : RK_LDG(in + r1 + xp)) : (T)0;
-        v[r] = ok ? cmk(x0 * mask_of<T>(a.in_mask, r0 + xp), x1 * mask_of<T>(a.in_mask, r1 + xp)) : cmk((T)0, (T)0);
+        const T x1 = ok1 ? (bulk ? rb[xp] : RK_LDG(in + r1 + xp)) : (T)0;
+        v[r] = ok ? cmk(x0 * mask_of<T>(a.in_mask, r0 + xp), ok1 ? x1 * mask_of<T>(a.in_mask, r1 + xp) : (T)0)
+                  : cmk((T)0, (T)0);
       }
     }
     F::forward(v, t, buf, a.tw);
@@ -606,7 +613,7 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
         for (int r = 0; r < X::R; ++r) {
           const int xp = F::nat_pos(t, r);
           out[r0 + xp] = w[r].x * mask_of<T>(a.out_mask, r0 + xp);
-          out[r1 + xp] = w[r].y * mask_of<T>(a.out_mask, r1 + xp);
+          if (ok1) out[r1 + xp] = w[r].y * mask_of<T>(a.out_mask, r1 + xp);
         }
     }
   }
@@ -619,8 +626,10 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_merge(const Pass
   RK_DYN_SMEM(cpx<T>, sm);
   const int t = threadIdx.x % X::P, l = threadIdx.x / X::P;
   const long long q = (long long)blockIdx.x * LX + l;
-  const long long npairs = ((long long)a.ny * a.nz) / 2;
+  const long long nrows_all = (long long)a.ny * a.nz;
+  const long long npairs = (nrows_all + 1) / 2;  // an odd last row pairs with a row of zeros
   const bool ok = q < npairs;
+  const bool ok1 = 2 * q + 1 < nrows_all;
   const long long r0 = 2 * q * a.nx, r1 = r0 + a.nx;
   typename X::B buf{sm + (size_t)l * X::B::SIZE};
   cpx<T> v[X::R], acc[X::R];
@@ -633,7 +642,7 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_merge(const Pass
 #pragma unroll
       for (int r = 0; r < X::R; ++r) {
         const int xp = F::nat_pos(t, r);
-        v[r] = ok ? cmk(RK_LDG(in + r0 + xp), RK_LDG(in + r1 + xp)) : cmk((T)0, (T)0);
+        v[r] = cmk(ok ? RK_LDG(in + r0 + xp) : (T)0, ok1 ? RK_LDG(in + r1 + xp) : (T)0);
       }
       F::forward(v, t, buf, a.tw);
 #pragma unroll
@@ -664,7 +673,7 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_merge(const Pass
       for (int r = 0; r < X::R; ++r) {
         const int xp = F::nat_pos(t, r);
         out[r0 + xp] = acc[r].x;
-        out[r1 + xp] = acc[r].y;
+        if (ok1) out[r1 + xp] = acc[r].y;
       }
     if (a.cg_p) {
       DotAccPair<T> dot;
@@ -672,7 +681,7 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_merge(const Pass
 #pragma unroll
         for (int r = 0; r < X::R; ++r) {
           const int xp = F::nat_pos(t, r);
-          dot.add(cmk(a.cg_p[r0 + xp], a.cg_p[r1 + xp]), acc[r]);
+          dot.add(cmk(a.cg_p[r0 + xp], ok1 ? a.cg_p[r1 + xp] : (T)0), acc[r]);
         }
       cg_pap_reduce<X::THREADS>(dot.value(), a);
     }

@@ -420,7 +420,8 @@ cudaError_t launch_pointwise_stiff(const PointwiseArgs<T>& a, cudaStream_t s) {
   const long long nb = (a.nbox / VEC + 255) / 256;
   const unsigned grid = (unsigned)(nb < 152 * 16 ? (nb > 0 ? nb : 1) : 152 * 16);
   count_launch();
-  switch (a.s) {  // 3D bases (4, 10 monomials) and 2D bases (3, 6)
+  switch (a.s) {  // 3D bases (4, 10 monomials), 2D bases (3, 6) and 1D bases (2, 3)
+    case 2: k_pointwise_stiff<T, 2><<<grid, 256, 0, s>>>(a); break;
     case 4: k_pointwise_stiff<T, 4><<<grid, 256, 0, s>>>(a); break;
     case 10: k_pointwise_stiff<T, 10><<<grid, 256, 0, s>>>(a); break;
     case 3: k_pointwise_stiff<T, 3><<<grid, 256, 0, s>>>(a); break;

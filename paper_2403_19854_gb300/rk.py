@@ -200,7 +200,8 @@ class Handle:
         self.n = tuple(int(v) for v in n)
         self.nbox = self.n[0] * self.n[1] * self.n[2]
         self.degree = int(degree)
-        self.s = (4 if degree == 1 else 10) if self.n[2] > 1 else (3 if degree == 1 else 6)  # 3D / 2D basis
+        dim = 3 if self.n[2] > 1 else (2 if self.n[1] > 1 else 1)
+        self.s = {3: (4, 10), 2: (3, 6), 1: (2, 3)}[dim][self.degree - 1]  # basis size of the box's dimension
         pc, kc = _ptr(chi)
         pg, kg = _ptr(chi_gamma)
         pV, kV = _ptr(V)

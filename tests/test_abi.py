@@ -67,9 +67,10 @@ def test_invalid_arguments_rejected_without_gpu(libpath):
 
 
 def test_grid_dimension_checks_without_gpu(libpath):
-    """A box one node thick in z is two-dimensional; one node thick in y (1D) is not
-    built (RK_ERR_UNSUPPORTED) and a first axis of one node is invalid -- all decided
-    before any device work."""
+    """A box one node thick in z is two-dimensional, one node thick in y and z
+    one-dimensional; a y axis of one node under a longer z axis, or a first axis of
+    one node, is invalid; a side that is not built, or a 1D side that is not a
+    multiple of 4, is unsupported -- all decided before any device work."""
     import ctypes
 
     from paper_2403_19854_gb300 import rk
@@ -79,9 +80,13 @@ def test_grid_dimension_checks_without_gpu(libpath):
     g = rk.Grid()
     for k in range(3):
         g.h[k] = 0.1
-    g.n[0], g.n[1], g.n[2] = 32, 1, 1
+    g.n[0], g.n[1], g.n[2] = 32, 1, 4        # n[1] == 1 < n[2]
+    assert L.rk_setup(ctypes.byref(g), dummy, None, dummy, 1, 1.5, None, ctypes.byref(out)) == 1
+    g.n[0], g.n[1], g.n[2] = 20, 1, 1        # 1D, a side that is not built
     assert L.rk_setup(ctypes.byref(g), dummy, None, dummy, 1, 1.5, None, ctypes.byref(out)) == 8
-    assert b"one-dimensional" in L.rk_last_error_message()
+    g.n[0], g.n[1], g.n[2] = 162, 1, 1       # 1D, built but not a multiple of 4
+    assert L.rk_setup(ctypes.byref(g), dummy, None, dummy, 1, 1.5, None, ctypes.byref(out)) == 8
+    assert b"multiple of 4" in L.rk_last_error_message()
     g.n[0], g.n[1], g.n[2] = 1, 32, 32
     assert L.rk_setup(ctypes.byref(g), dummy, None, dummy, 1, 1.5, None, ctypes.byref(out)) == 1
     g.n[0], g.n[1], g.n[2] = 32, 20, 1       # 2D, but a y side that is not built

@@ -96,12 +96,9 @@ def test_paper_2d_problem_converges_quadratically():
     assert np.all(rates > 1.9) and np.all(rates < 2.1), rates
 
 
-def test_2d_rejects_the_spectral_preconditioner_and_1d_grids():
+def test_2d_rejects_the_spectral_preconditioner():
     p = W.plane_problem(16, 1.5, 1)
     H = rk.Handle.from_problem(p, device=DEV)
     with pytest.raises(rk.RKError):
         H.apply_precond(tdev(W.random_field(p.nbox, 1)))
     H.close()
-    q = W.line_problem(32, 1.5, 1)
-    with pytest.raises(rk.RKError):
-        rk.Handle.from_problem(q, device=DEV)

@@ -46,7 +46,8 @@ def test_nonlinear_force(kind, deg, a):
     H.close()
 
 
-GRAD_CASES = [("cube", 16, 2.5, 1), ("cube", 16, 3.0, 2), ("spheres", 32, 2.5, 1), ("plane", 32, 2.5, 2)]
+GRAD_CASES = [("cube", 16, 2.5, 1), ("cube", 16, 3.0, 2), ("spheres", 32, 2.5, 1), ("plane", 32, 2.5, 2),
+              ("line", 64, 3.0, 2)]
 
 
 @pytest.mark.parametrize("kind", ["cubic", "sinh", "exp"])
@@ -59,11 +60,13 @@ def test_gradient_type_force_eq_b10(kind, geom, nb, a, deg):
         p = W.cube_problem(nb, a, deg, "sin")
     elif geom == "spheres":
         p = W.spheres_problem(n_box=nb, n_spheres=3, a_tilde=a, degree=deg, r_range=(0.2, 0.3), seed=8)
-    else:
+    elif geom == "plane":
         p = W.plane_problem(nb, a, deg)
+    else:
+        p = W.line_problem(nb, a, deg)
     H = rk.Handle.from_problem(p, device=DEV)
     o = Oracle(p.n, p.h, a, deg, p.chi)
-    av = [0.7, -1.3, 0.4 if p.n[2] > 1 else 0.0]
+    av = [0.7, -1.3 if p.n[1] > 1 else 0.0, 0.4 if p.n[2] > 1 else 0.0]
     d = 0.5 * W.random_field(p.nbox, 3) * p.chi
     u = o.eval_u(d)
     Nu = 2.0 * N[kind][0](u) * p.chi
