@@ -254,27 +254,22 @@ def pass_bytes(cls, w, s=4):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# kernels that can dominate a step, from one ncu capture of the 256^3-box cube
-# K.u (profiles/dram_Ku_f32_cube256.md).  A value holds only while the kernel is
-# unchanged: the sha256 of each listed source region (the kernel and its
-# argument struct) is checked at run time, and the traffic is null otherwise.
+# kernel that dominates a step, from one ncu capture of the 256^3-box cube K.u
+# (profiles/dram_zpass_f32_cube256.md; one-pass metrics on the full-size box).
+# A value holds only while the kernel is unchanged: the sha256 of each listed
+# source region (the kernel and its block shape) is checked at run time, and the
+# traffic is null otherwise.
 _PASSES = "paper_2403_19854_gb300/csrc/rk_passes.cuh"
 _STRIDED = (_PASSES, "template <typename T, int N, int L>\nstruct Strided {", "// PW > 0 (z SPLIT",
-            "7a4574a469839b2cdaca3f1a1c45af98b27fd3109511b5f6e8457a6417b15d14")
+            "650985d9545296426b74b48de165243a553705407e8d1c7b69a28f53a204202a")
 _MERGE_START = ("template <typename T, int N, int L>\n__global__ void __launch_bounds__(Strided<T, N, L>::THREADS, "
                 "Strided<T, N, L>::MIN_BLOCKS_MERGE)")
 MEASURED_TRAFFIC = {
-    ("z_split", "f32", 256): (202878208 + 210755328, [
-        _STRIDED,
-        (_PASSES, "// PW > 0 (z SPLIT", _MERGE_START,
-         "d5e51b6bc7d7509197db15a71b69eb846cdd73cf477f7041bafff3a4179309f8"),
-        ("paper_2403_19854_gb300/csrc/rk_pointwise.cuh", "// rk_pointwise.cuh", "}  // namespace rk",
-         "9bbfd8b1f836022992c4b6b4ea5a93dc93f98c10454a65cfd19c154923b3e842"),
-    ]),
-    ("z_merge", "f32", 256): (268490240 + 152869376, [
+    # the z pass (regular part of the z axis, 3 fields in, 3 out)
+    ("z_merge", "f32", 256): (201375744 + 150393088, [
         _STRIDED,
         (_PASSES, _MERGE_START, "// ------------------------------------------------------------------- x passes",
-         "ed2892cc26badc1fa71f36903b97f8c638c1b366febd3bf05cff16e0ed367043"),
+         "3118cebc6002bfa18b32bad4314d39dcabd39f439d3acb0f36b065e590c7ebaa"),
     ]),
 }
 
@@ -554,6 +549,15 @@ def run_ours(args):
     h2d = p.nbox * (1 + 1 + 8 + 8 + 8)
     d2h = p.nbox * (8 + 8)
 
+    # the batched workload (uneven embedded domains, several right-hand sides), small
+    # enough for the default run: one rk_solve_batched, spectral PCG
+    batched = None
+    if args.batched_domains > 0 and world == 1:
+        b = batched_core(args.batched_domains, 1e-10, 2000, "spectral", 1, 20240328 + 5000, dev, local, world)
+        batched = {"value": b["units_local"] / (b["ms_local"] / 1e3), "unit": "DOF/s", "ms_per_step": b["ms_local"],
+                   "config": b["config"], "per_degree": b["per_degree"], "launch_groups": b["launch_stats"],
+                   "gpu_launches": b["launches"]}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, _, nt = oracle_kd_rate()
@@ -581,6 +585,7 @@ def run_ours(args):
             "cufft_comparison": cufft,
             "appendix_ops": appendix,
             "spheres256_quadratic": spheres,
+            "batched": batched,
             "profiled_step_ms": profiled_ms,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -597,22 +602,20 @@ def run_ours(args):
     return 0
 
 
-def run_batched(args):
+def batched_core(domains, tol, max_iter, precond, steps, seed, dev, local, world):
     """Batched solves of uneven embedded domains: seeded domains of box side
     U{32..160} (1-12 spheres, linear a = 2.5h or quadratic a = 3.0h), 4 right-hand
     sides each, every domain padded to the built FFT side the autotuner measures
     fastest; one step = one rk_solve_batched of all (domain, right-hand side) items
-    (mixed precision, a fixed iteration budget per item)."""
+    (mixed precision, a fixed iteration budget per item).  Returns the measured
+    quantities (rank-local ms; units aggregated by the caller)."""
     import numpy as np
     import torch
     from paper_2403_19854_gb300 import autotune, rk
     from paper_2403_19854_gb300 import workloads as W
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     rk.lib()
-    doms = W.batched_domains(n_domains=args.domains, n_rhs=4, seed=20240328 + 5000 + 97 * rank)
+    doms = W.batched_domains(n_domains=domains, n_rhs=4, seed=seed)
     items, handles, skipped = [], [], 0
     for p0, rhs in doms:
         free, _ = torch.cuda.mem_get_info()
@@ -630,8 +633,8 @@ def run_batched(args):
             items.append({"p": p, "S": p0.n[0], "h": h, "r": torch.as_tensor(rp, device=dev),
                           "g": torch.as_tensor(p.g, device=dev),
                           "d": torch.empty(p.nbox, dtype=torch.float64, device=dev)})
-    opts = rk.default_opts(precision="mixed", tol=args.tol, check_every=16, max_iter=args.max_iter, fp64_finish=0,
-                           precond=args.precond)
+    opts = rk.default_opts(precision="mixed", tol=tol, check_every=16, max_iter=max_iter, fp64_finish=0,
+                           precond=precond)
     batch = [(it["h"], it["r"], it["g"], it["d"], None) for it in items]
     rk.solve_batched(batch, opts=opts, raise_on_error=False)  # warm-up: graphs, tables
     stream = torch.cuda.current_stream()
@@ -642,7 +645,7 @@ def run_batched(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     infos = None
-    for _ in range(args.steps):
+    for _ in range(steps):
         infos = rk.solve_batched(batch, opts=opts, raise_on_error=False)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -650,7 +653,6 @@ def run_batched(args):
     clocks = clk.stop()
     ms_local = e0.elapsed_time(e1)
     units_local = float(sum(it["p"].n_omega * (i["matvec_f32"] + i["matvec_f64"]) for it, i in zip(items, infos)))
-    ms, units = aggregate_over_ranks(ms_local, units_local * args.steps, world, dev)
     per_deg = {}
     for it, i in zip(items, infos):
         dd = per_deg.setdefault(f"degree{it['p'].degree}", {"items": 0, "converged": 0, "iterations": [], "rel": []})
@@ -664,28 +666,42 @@ def run_batched(args):
         dd["median_rel_residual"] = float(np.median(rel))
         dd["worst_rel_residual"] = float(np.max(rel))
     max_it = max(i["iterations"] for i in infos)
-    launch_stats = {"gpu_launches_per_step": int((L1 - L0) / args.steps),
-                    "launches_per_cg_iteration_of_the_batch": (L1 - L0) / args.steps / max(max_it, 1),
-                    "max_iterations": int(max_it)}
-    if rank == 0:
-        sides = sorted({(it["S"], it["p"].n[0]) for it in items})
-        line = {"metric": "batched DOF x K.u applications per second (uneven domains, mixed precision)",
-                "value": units / (ms / 1e3), "unit": "DOF/s", "n_gpus": world, "steps": args.steps, "warmup": 1,
-                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": f"batched {len(handles)} domains x 4 rhs", "domains": len(handles),
-                           "skipped_for_memory": skipped, "items": len(items), "tol": args.tol,
-                           "max_iter": args.max_iter, "precond": args.precond,
-                           "box_nodes": int(sum(it["p"].nbox for it in items)),
-                           "dof": int(sum(it["p"].n_omega for it in items)),
-                           "padded_sides": [list(v) for v in sides]},
-                "per_degree": per_deg, "launch_groups": launch_stats, "clocks": clocks,
-                "gpu_launches": int(L1 - L0)}
-        print(json.dumps(line), flush=True)
+    out = {"ms_local": ms_local, "units_local": units_local * steps, "clocks": clocks,
+           "launches": int(L1 - L0), "per_degree": per_deg,
+           "launch_stats": {"gpu_launches_per_step": int((L1 - L0) / steps),
+                            "launches_per_cg_iteration_of_the_batch": (L1 - L0) / steps / max(max_it, 1),
+                            "max_iterations": int(max_it)},
+           "config": {"domains": len(handles), "skipped_for_memory": skipped, "items": len(items), "tol": tol,
+                      "max_iter": max_iter, "precond": precond,
+                      "box_nodes": int(sum(it["p"].nbox for it in items)),
+                      "dof": int(sum(it["p"].n_omega for it in items)),
+                      "padded_sides": [list(v) for v in sorted({(it["S"], it["p"].n[0]) for it in items})]}}
     for hs in handles:
         for h in hs[1:]:
             h.close()
         hs[0].close()
+    return out
+
+
+def run_batched(args):
+    """The batched workload on its own line (batched_core)."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    b = batched_core(args.domains, args.tol, args.max_iter, args.precond, args.steps,
+                     20240328 + 5000 + 97 * rank, dev, local, world)
+    ms, units = aggregate_over_ranks(b["ms_local"], b["units_local"], world, dev)
+    if rank == 0:
+        cfg = dict(b["config"])
+        cfg["workload"] = f"batched {cfg['domains']} domains x 4 rhs"
+        line = {"metric": "batched DOF x K.u applications per second (uneven domains, mixed precision)",
+                "value": units / (ms / 1e3), "unit": "DOF/s", "n_gpus": world, "steps": args.steps, "warmup": 1,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic", "config": cfg, "per_degree": b["per_degree"],
+                "launch_groups": b["launch_stats"], "clocks": b["clocks"], "gpu_launches": b["launches"]}
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -709,6 +725,8 @@ def main():
     ap.add_argument("--degree", type=int, default=1, choices=[1, 2], help="ku: basis degree")
     ap.add_argument("--reps", type=int, default=4, help="ku: number of K.u")
     ap.add_argument("--domains", type=int, default=64, help="batched: number of domains")
+    ap.add_argument("--batched-domains", type=int, default=16,
+                    help="domains of the batched key of the default line (0: none)")
     ap.add_argument("--max-iter", type=int, default=2000, help="batched: CG iterations per item")
     ap.add_argument("--precond", default="none", choices=["none", "spectral"], help="batched: preconditioner")
     args = ap.parse_args()
