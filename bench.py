@@ -316,14 +316,26 @@ def run_ours(args):
     g = torch.as_tensor(p.g, device=dev)
     d = torch.empty(p.nbox, dtype=torch.float64, device=dev)
     u = torch.empty_like(d)
+    # the replacement settings of the mixed solve, measured on this problem
+    # (autotune.best_mixed_opts: one solve per candidate before the warm-up)
+    from paper_2403_19854_gb300 import autotune
+    Ht = rk.Handle(p.n, p.h, chi, cg, V, 1, 2.5)
+    itol, ce, tune_t = autotune.best_mixed_opts(Ht, r, g, tol=args.tol)
+    Ht.close()
+    # the timed steps use the library's default settings (value = K.u throughput at
+    # those); the tuned settings' time-to-solve is one extra step, reported beside it
     opts = rk.default_opts(precision="mixed", tol=args.tol)
+    opts_tuned = rk.default_opts(precision="mixed", tol=args.tol, inner_tol=itol, check_every=ce)
+    solver_opts = {"timed_steps": {"inner_tol": opts.inner_tol, "check_every": opts.check_every},
+                   "autotuned": {"inner_tol": itol, "check_every": ce, "chosen_by": "autotune.best_mixed_opts",
+                                 "candidates_s_iterations_status": tune_t}}
     stream = torch.cuda.current_stream()
 
-    def step(prof=False):
+    def step(prof=False, o=None):
         H = rk.Handle(p.n, p.h, chi, cg, V, 1, 2.5)
         if prof:
             H.profile(True)
-        _, _, info = H.solve(r, g, d, u, opts=opts)
+        _, _, info = H.solve(r, g, d, u, opts=o if o is not None else opts)
         pr = H.profile_read() if prof else None
         H.close()
         return info, pr
@@ -363,6 +375,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     profiled_ms = p0.elapsed_time(p1)
     profs = [pr]
+    # one more step, not in the timed region: the mixed solve with the tuned settings
+    q0 = torch.cuda.Event(enable_timing=True)
+    q1 = torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    info_tuned, _ = step(o=opts_tuned)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    solver_opts["autotuned"].update({"time_to_solve_s": q0.elapsed_time(q1) / 1e3,
+                                     "iterations": info_tuned["iterations"], "status": info_tuned["status"]})
     matvecs = sum(i["matvec_f32"] + i["matvec_f64"] for i in infos)
     ms, units = aggregate_over_ranks(ms_local, float(n_dof * matvecs), world, dev)
     value = units / (ms / 1e3)
@@ -465,6 +486,22 @@ def run_ours(args):
         torch.cuda.synchronize()
         spheres[f"kU_{dt_name}_ms"] = a0.elapsed_time(a1) / reps
         del x, y
+    # time to a common reachable residual: direct nodal integration with the
+    # quadratic basis keeps near-zero-energy modes, so neither precision gets far
+    # below 1e-2 in a few thousand iterations; both solves use the spectral
+    # preconditioner (plain FP64 CG does not reach 1e-2 in 3000 iterations)
+    if args.spheres_solve:
+        rs, gs = torch.as_tensor(sph.r, device=dev), torch.as_tensor(sph.g, device=dev)
+        sol = {"tol": 1e-2, "precond": "spectral"}
+        for prec in ("mixed", "fp64"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, si = Hs.solve(rs, gs, precision=prec, tol=1e-2, precond="spectral", max_iter=4000, fp64_finish=0,
+                                raise_on_error=False)
+            torch.cuda.synchronize()
+            sol[prec] = {"time_to_solve_s": time.perf_counter() - t0, "iterations": si["iterations"],
+                         "rel_residual": si["rel_residual"], "status": si["status"]}
+        spheres["solve_to_1e-2"] = sol
     Hs.close()
     del sph
 
@@ -573,8 +610,10 @@ def run_ours(args):
             "config": {"workload": f"cube{args.size}-linear-a2.5-sin", "box": list(p.n), "n_omega": n_dof,
                        "degree": 1, "a_tilde": 2.5, "precision": "mixed (FP32 K.u, FP64 dots/refinement)",
                        "tol": args.tol, "l2": "inputs and working set larger than L2 (no flush needed)",
-                       "parallelism": f"replicas x{world}"},
-            "time_to_solve_s": {"mixed": ms / args.steps / 1e3, "fp64": fp64["time_to_solve_s"] if fp64 else None,
+                       "parallelism": f"replicas x{world}", "mixed_solver": solver_opts},
+            "time_to_solve_s": {"mixed": ms / args.steps / 1e3,
+                                "mixed_autotuned": solver_opts["autotuned"]["time_to_solve_s"],
+                                "fp64": fp64["time_to_solve_s"] if fp64 else None,
                                 "mixed_pcg": pcg["mixed"]["time_to_solve_s"], "fp64_pcg": pcg["fp64"]["time_to_solve_s"]},
             "pcg_solve": pcg,
             "solve": {"iterations": infos[-1]["iterations"], "outer": infos[-1]["outer"],
@@ -725,6 +764,8 @@ def main():
     ap.add_argument("--degree", type=int, default=1, choices=[1, 2], help="ku: basis degree")
     ap.add_argument("--reps", type=int, default=4, help="ku: number of K.u")
     ap.add_argument("--domains", type=int, default=64, help="batched: number of domains")
+    ap.add_argument("--spheres-solve", type=int, default=1,
+                    help="time the 12-spheres quadratic solves (mixed and FP64 PCG to 1e-2; about 45 s)")
     ap.add_argument("--batched-domains", type=int, default=16,
                     help="domains of the batched key of the default line (0: none)")
     ap.add_argument("--max-iter", type=int, default=2000, help="batched: CG iterations per item")

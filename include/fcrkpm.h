@@ -128,8 +128,10 @@ int rk_supported_length(int n);
  * and FP32, plus chi*V (Eq. 87).
  *   grid       box size and spacing; n[2] == 1 makes the problem two-dimensional
  *              (Sec. 6.1.2: no z axis, kernel phi(x)phi(y), basis [1, x, y] or
- *              [1, x, y, x^2, xy, y^2], b^z = 0, V the 2D cell measure); n[1] == 1
- *              (1D) is not built
+ *              [1, x, y, x^2, xy, y^2], b^z = 0, V the 2D cell measure); n[1] ==
+ *              n[2] == 1 makes it one-dimensional (Sec. 6.1.1: kernel phi(x), basis
+ *              [1, x] or [1, x, x^2], b^y = b^z = 0, V the 1D cell length; n[0] a
+ *              multiple of 4); n[0] == 1, or n[1] == 1 < n[2], is invalid
  *   chi        uint8[nbox], Eq. 40
  *   chi_gamma  uint8[nbox], Eq. 95 (NULL: no Dirichlet nodes)
  *   V          double[nbox], nodal volumes of direct nodal integration (Eq. 54, 87)
@@ -138,7 +140,7 @@ int rk_supported_length(int n);
  *   stream     cudaStream_t for the set-up work (synchronised before return)
  *   out        receives the handle
  * Errors: RK_ERR_INVALID_ARG, RK_ERR_UNSUPPORTED (size not built, odd sizes, gap
- * narrower than Eq. 66, 1D grid), RK_ERR_OOM, RK_ERR_CUDA, RK_ERR_SINGULAR_MOMENT (the
+ * narrower than Eq. 66, a 1D side not a multiple of 4), RK_ERR_OOM, RK_ERR_CUDA, RK_ERR_SINGULAR_MOMENT (the
  * handle is still returned; rk_singular_nodes gives the count and first node).
  */
 rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_gamma, const double* V,

@@ -1,4 +1,5 @@
-"""Padded box sides for uneven domains, chosen by measurement.
+"""Padded box sides for uneven domains, and the replacement settings of the mixed
+solve for a given problem, chosen by measurement.
 
 A domain of side S can be solved in any built FFT box side S' >= S (the extra
 nodes lie outside the domain, chi = 0).  For each candidate S' this module times
@@ -76,3 +77,40 @@ def best_side(S, degree, max_candidates=3):
     if changed:
         _save(cache)
     return best
+
+
+# Residual-replacement settings of the mixed solve (inner_tol, check_every): the
+# FP32 recurrence is replaced by the true FP64 residual each time it has dropped
+# by inner_tol, checked every check_every iterations.  Which setting needs the
+# fewest iterations depends on the problem, irregularly (a replacement resets the
+# rounding the FP32 recurrence has gathered), so it is measured.
+MIXED_CANDIDATES = ((0.1, 25), (0.5, 10), (0.3, 10))
+
+
+def best_mixed_opts(handle, r, g, tol=1e-10, candidates=MIXED_CANDIDATES, precond="none"):
+    """Time one mixed solve of (r, g) on handle per candidate (inner_tol,
+    check_every) and return (inner_tol, check_every, {candidate: (seconds,
+    iterations, status)}).  A candidate may use at most twice the iterations of
+    the first one; one that does not reach tol is not chosen."""
+    import time
+
+    import torch
+    timings = {}
+    best, best_t, cap = None, None, None
+    for itol, ce in candidates:
+        kw = dict(precision="mixed", tol=tol, inner_tol=itol, check_every=ce, precond=precond)
+        if cap is not None:
+            kw["max_iter"] = cap
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, info = handle.solve(r, g, raise_on_error=False, **kw)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        timings[f"{itol}/{ce}"] = (t, info["iterations"], info["status"])
+        if cap is None:
+            cap = 2 * max(info["iterations"], 1)
+        if info["status"] == 0 and (best_t is None or t < best_t):
+            best, best_t = (itol, ce), t
+    if best is None:
+        best = candidates[0]
+    return best[0], best[1], timings

@@ -226,3 +226,21 @@ def test_autotune_picks_a_built_side():
     S = 37
     n = autotune.best_side(S, 1, max_candidates=2)
     assert n >= S and rk.supported_length(n)
+
+
+def test_autotune_mixed_opts_picks_a_converging_candidate():
+    """autotune.best_mixed_opts times one mixed solve per replacement setting and
+    returns the fastest one that reached tol; the solve with it matches the oracle."""
+    from paper_2403_19854_gb300 import autotune
+    p = W.cube_problem(16, 2.0, 1, "sin")
+    H = rk.Handle.from_problem(p, device=DEV)
+    r, g = tdev(p.r), tdev(p.g)
+    itol, ce, t = autotune.best_mixed_opts(H, r, g, tol=1e-12)
+    assert (itol, ce) in autotune.MIXED_CANDIDATES
+    assert len(t) == len(autotune.MIXED_CANDIDATES)
+    assert t[f"{itol}/{ce}"][2] == 0
+    d, _, info = H.solve(r, g, precision="mixed", tol=1e-12, inner_tol=itol, check_every=ce)
+    o = Oracle(p.n, p.h, p.a_tilde, p.degree, p.chi)
+    do, _ = o.solve(p.V, p.chi_gamma, p.r, p.g, tol=1e-14)
+    assert rel(np_(d), do) < 1e-9
+    H.close()
