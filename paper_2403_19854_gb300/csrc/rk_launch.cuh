@@ -135,11 +135,20 @@ cudaError_t merge_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMa
     using X = XPass<T, N, LX>;
     const long long npairs = ((long long)a.ny * a.nz + 1) / 2;  // an odd last row pairs with zeros
     const unsigned nb = (unsigned)((npairs + LX - 1) / LX);
-    auto k = k_x_merge<T, N, LX>;
-    cudaError_t e = set_smem(k, X::SMEM);
-    if (e != cudaSuccess) return e;
-    count_launch();
-    k<<<nb, X::THREADS, X::SMEM, s>>>(a);
+    auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) % 16) == 0; };
+    if (X::MERGE_BULK && a.cg_p && a.n_groups == 1 && aligned(a.cg_p) && (!a.out_mask || aligned(a.out_mask))) {
+      auto k = k_x_merge<T, N, LX, true>;
+      cudaError_t e = set_smem(k, X::SMEM_MERGE_FEED);
+      if (e != cudaSuccess) return e;
+      count_launch();
+      k<<<nb, X::THREADS, X::SMEM_MERGE_FEED, s>>>(a);
+    } else {
+      auto k = k_x_merge<T, N, LX, false>;
+      cudaError_t e = set_smem(k, X::SMEM);
+      if (e != cudaSuccess) return e;
+      count_launch();
+      k<<<nb, X::THREADS, X::SMEM, s>>>(a);
+    }
   } else {
     return launch_strided<T, N, true>(axis, a, s, maps);
   }

@@ -394,8 +394,20 @@ struct XPass {
   static constexpr int PITCH = N + 32 / (int)sizeof(T);
   static constexpr size_t TILE = sizeof(T) * (size_t)ROWS * PITCH;
   static constexpr size_t SMEM_FEED = SMEM > 2 * TILE ? SMEM : 2 * TILE;
-  // resident blocks per SM the register allocation must allow
-  static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 4 : 3;
+  // Bulk feed of the CG x merge: the block's rows of p (for p . Ap) and of the
+  // output mask land in shared memory behind the transpose buffer while the block
+  // transforms, so the epilogue reads neither from HBM.  Possible when a mask row
+  // is a whole number of 16-byte units as well.
+  static constexpr bool MERGE_BULK = BULK && N % 16 == 0;
+  static constexpr size_t MASK_TILE = (size_t)ROWS * N;
+  static constexpr size_t SMEM_MERGE_FEED = SMEM + TILE + MASK_TILE;
+  // resident blocks per SM the register allocation must allow.  FP32 lines of at
+  // most 12 values per thread, and N = 256: 5 blocks of 128 threads (102
+  // registers; at N = 256 against 4 blocks: x split 64.2 -> 63.2 us, x merge
+  // 82.1 -> 75.3 us); longer lines per thread keep the budget they need.
+  static constexpr bool FIVE = sizeof(T) == 4 && (R <= 12 || N == 256);
+  static constexpr int MIN_BLOCKS = FIVE ? 5 : (sizeof(T) == 4 ? 4 : 3);
+  static constexpr int MIN_BLOCKS_MERGE = FIVE ? 5 : 1;
 };
 
 RK_DEV void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -559,6 +571,48 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
   }
   const T* ra = tileA + (2 * l) * X::PITCH;  // this thread's rows in the tiles
   const T* rb = ra + X::PITCH;
+  if (FEED && bulk && a.cg_r) {
+    // the CG prologue from the row tiles, one group, outputs unmasked or masked
+    const T be = (T)a.cg->beta;
+    const T* pa = tileB + (2 * l) * X::PITCH;
+#pragma unroll
+    for (int r = 0; r < X::R; ++r) {
+      const int xp = F::nat_pos(t, r);
+      T p0 = (T)0, p1 = (T)0;
+      if (ok) {
+        p0 = ra[xp] + be * pa[xp];
+        if (ok1) p1 = rb[xp] + be * pa[X::PITCH + xp];
+        a.cg_p[r0 + xp] = p0;
+        if (ok1) a.cg_p[r1 + xp] = p1;
+      }
+      v[r] = cmk(p0, p1);
+    }
+    F::forward(v, t, buf, a.tw);
+    for (int qq = a.g_begin[0]; qq < a.g_begin[1]; ++qq) {
+      const int m = a.term_m[qq];
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) w[r] = spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
+      F::inverse(w, t, buf, a.tw);
+      T* out = a.out[a.term_io[qq]];
+      if (!ok) continue;
+      if (a.out_mask) {
+#pragma unroll
+        for (int r = 0; r < X::R; ++r) {
+          const int xp = F::nat_pos(t, r);
+          out[r0 + xp] = w[r].x * (T)RK_LDG(a.out_mask + r0 + xp);
+          if (ok1) out[r1 + xp] = w[r].y * (T)RK_LDG(a.out_mask + r1 + xp);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < X::R; ++r) {
+          const int xp = F::nat_pos(t, r);
+          out[r0 + xp] = w[r].x;
+          if (ok1) out[r1 + xp] = w[r].y;
+        }
+      }
+    }
+    return;
+  }
   for (int g = 0; g < a.n_groups; ++g) {
     const T* in = a.in[a.g_io[g]];
     if (a.cg_r) {
@@ -619,11 +673,15 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
   }
 }
 
-template <typename T, int N, int LX>
-__global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_merge(const PassArgs<T> a) {
+// FEED: the CG variant (one group, p . Ap epilogue) with the block's rows of p and
+// of the output mask arriving by bulk async copies while the block transforms.
+template <typename T, int N, int LX, bool FEED>
+__global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN_BLOCKS_MERGE)
+    k_x_merge(const PassArgs<T> a) {
   using X = XPass<T, N, LX>;
   using F = typename X::F;
-  RK_DYN_SMEM(cpx<T>, sm);
+  RK_DYN_SMEM(unsigned char, smem);
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem);
   const int t = threadIdx.x % X::P, l = threadIdx.x / X::P;
   const long long q = (long long)blockIdx.x * LX + l;
   const long long nrows_all = (long long)a.ny * a.nz;
@@ -633,6 +691,75 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS) k_x_merge(const Pass
   const long long r0 = 2 * q * a.nx, r1 = r0 + a.nx;
   typename X::B buf{sm + (size_t)l * X::B::SIZE};
   cpx<T> v[X::R], acc[X::R];
+  if (FEED) {
+    T* ptile = reinterpret_cast<T*>(smem + X::SMEM);
+    uint8_t* mtile = smem + X::SMEM + X::TILE;
+    __shared__ uint64_t bar;
+    const long long row0 = 2LL * blockIdx.x * LX;
+    const int rows = (int)((nrows_all - row0) < X::ROWS ? (nrows_all - row0) : X::ROWS);
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      mbar_init_fence();
+    }
+    RK_SYNC();
+    if (threadIdx.x < 32) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar, (uint32_t)(rows * N * sizeof(T) + (a.out_mask ? rows * N : 0)));
+      }
+      __syncwarp();
+      for (int j = threadIdx.x; j < rows; j += 32)
+        bulk_g2s(ptile + j * X::PITCH, a.cg_p + (row0 + j) * N, (uint32_t)(N * sizeof(T)), &bar);
+      if (threadIdx.x == 0 && a.out_mask) bulk_g2s(mtile, a.out_mask + row0 * N, (uint32_t)(rows * N), &bar);
+    }
+#pragma unroll
+    for (int r = 0; r < X::R; ++r) acc[r] = cmk((T)0, (T)0);
+    for (int qq = a.g_begin[0]; qq < a.g_begin[1]; ++qq) {
+      const T* in = a.in[a.term_io[qq]];
+      const int m = a.term_m[qq];
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) {
+        const int xp = F::nat_pos(t, r);
+        v[r] = cmk(ok ? RK_LDG(in + r0 + xp) : (T)0, ok1 ? RK_LDG(in + r1 + xp) : (T)0);
+      }
+      F::forward(v, t, buf, a.tw);
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) acc[r] = acc[r] + spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
+    }
+    F::inverse(acc, t, buf, a.tw);
+    // the tiles: bounded wait; on a time-out the block records it, waits (bounded)
+    // for the copies still in flight and writes nothing, but still takes part in
+    // the p . Ap reduction (with 0), so that its counter ends the launch reset
+    const bool got = mbar_wait(&bar, 0u, a.short_wait ? 0u : kWaitLimit);
+    if (__syncthreads_or(!got)) {
+      if (threadIdx.x == 0) flag_wait_error(a.err);
+      mbar_wait(&bar, 0u);
+      cg_pap_reduce<X::THREADS>(0.0, a);
+      return;
+    }
+    if (a.out_mask) {
+      const uint8_t* mk = mtile + (2 * l) * N;
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) {
+        const int xp = F::nat_pos(t, r);
+        acc[r] = pmul(acc[r], cmk((T)mk[xp], ok1 ? (T)mk[N + xp] : (T)0));
+      }
+    }
+    T* out = a.out[a.g_io[0]];
+    DotAccPair<T> dot;
+    if (ok) {
+      const T* pa = ptile + (2 * l) * X::PITCH;
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) {
+        const int xp = F::nat_pos(t, r);
+        out[r0 + xp] = acc[r].x;
+        if (ok1) out[r1 + xp] = acc[r].y;
+        dot.add(cmk(pa[xp], ok1 ? pa[X::PITCH + xp] : (T)0), acc[r]);
+      }
+    }
+    cg_pap_reduce<X::THREADS>(dot.value(), a);
+    return;
+  }
   for (int g = 0; g < a.n_groups; ++g) {
 #pragma unroll
     for (int r = 0; r < X::R; ++r) acc[r] = cmk((T)0, (T)0);
