@@ -262,14 +262,17 @@ def pass_bytes(cls, w, s=4):
 _PASSES = "paper_2403_19854_gb300/csrc/rk_passes.cuh"
 _STRIDED = (_PASSES, "template <typename T, int N, int L>\nstruct Strided {", "// PW > 0 (z SPLIT",
             "650985d9545296426b74b48de165243a553705407e8d1c7b69a28f53a204202a")
-_MERGE_START = ("template <typename T, int N, int L>\n__global__ void __launch_bounds__(Strided<T, N, L>::THREADS, "
-                "Strided<T, N, L>::MIN_BLOCKS_MERGE)")
+_SPLIT_START = ("template <typename T, int N, int L, int PW>\n__global__ void __launch_bounds__(Strided<T, N, L>::THREADS, "
+                "Strided<T, N, L>::MIN_BLOCKS_SPLIT)")
+_MERGE_START = "template <typename T, int N, int L>\n__global__ void __launch_bounds__(Strided<T, N, L>::THREADS, "
+_API = "paper_2403_19854_gb300/csrc/rk_api.cu"
 MEASURED_TRAFFIC = {
-    # the z pass (regular part of the z axis, 3 fields in, 3 out)
-    ("z_merge", "f32", 256): (201375744 + 150393088, [
+    # the z pass (regular part of the z axis, 3 fields in, 3 out) on the split kernel
+    ("z_merge", "f32", 256): (201385472 + 144517120, [
         _STRIDED,
-        (_PASSES, _MERGE_START, "// ------------------------------------------------------------------- x passes",
-         "3118cebc6002bfa18b32bad4314d39dcabd39f439d3acb0f36b065e590c7ebaa"),
+        (_PASSES, _SPLIT_START, _MERGE_START, "c68852f1a89adb44417aa6fbff51d6c92e9eccbfd5e40db56c6d0249da4d1bd0"),
+        (_API, "    // Every group has one multiplier at most, so the pass is split-shaped",
+         "    {\n      ProfScope ps(h, prof_cls<T>(RK_PROF_Z_STIFF), s);", "94d721f4d25a9cdae6710882bb5af1f3683c567f0edb2804743e02eb3ee4396e"),
     ]),
 }
 

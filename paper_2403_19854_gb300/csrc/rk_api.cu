@@ -395,8 +395,9 @@ bool tile_maps_for(rk_handle* h, int axis, const PassArgs<T>& a, TileMaps* tm) {
 // pw: the z SPLIT of Alg. 2 also applies the pointwise stage to the regular nodes
 template <typename T>
 rk_status run_split(rk_handle* h, int axis, const PassArgs<T>& a, cudaStream_t s,
-                    const PointwiseArgs<T>* pw = nullptr) {
-  ProfScope ps(h, prof_cls<T>(axis == 0 ? RK_PROF_X_SPLIT : (axis == 1 ? RK_PROF_Y_SPLIT : RK_PROF_Z_SPLIT)), s);
+                    const PointwiseArgs<T>* pw = nullptr, int prof = -1) {
+  ProfScope ps(h, prof_cls<T>(prof >= 0 ? prof : (axis == 0 ? RK_PROF_X_SPLIT : (axis == 1 ? RK_PROF_Y_SPLIT : RK_PROF_Z_SPLIT))),
+               s);
   TileMaps tm;
   const bool use = tile_maps_for<T>(h, axis, a, &tm);
   cudaError_t e = launch_split<T>(axis, h->n[axis], a, s, use ? &tm : nullptr, pw);
@@ -643,23 +644,30 @@ rk_status op_K(rk_handle* h, const T* d, T* f, const uint8_t* in_mask, const uin
     // the z axis as its regular part -- one spectral pass, E_g -> G_g with the
     // multiplier c n |T^|^2 of the group's gradient basis function (none: G_g = 0)
     // -- and the local corrections of the non-regular nodes (rk_zcorr.cuh)
+    // Every group has one multiplier at most, so the pass is split-shaped (one
+    // transform in, one product, one transform out per group) and runs on the
+    // split kernel, which holds no accumulator and keeps three blocks per SM; the
+    // outputs of the groups without a multiplier are set to 0.
     PassArgs<T> rg = pass_base<T>(h, 2);
     rg.coef_rows = h->zrows;
-    rg.n_groups = c.nY;
-    int nt = 0;
+    int ng = 0;
     for (int g = 0; g < c.nY; ++g) {
-      rg.in[g] = h->ws<T>(c.nX + g);
-      rg.out[g] = h->ws<T>(c.nX + c.nY + g);
-      rg.g_io[g] = g;
-      rg.g_begin[g] = nt;
-      if (h->zreg_row[g] >= 0) {
-        rg.term_io[nt] = g;
-        rg.term_m[nt] = h->zreg_row[g];
-        ++nt;
+      T* out = h->ws<T>(c.nX + c.nY + g);
+      if (h->zreg_row[g] < 0) {
+        RK_CK(cudaMemsetAsync(out, 0, sizeof(T) * (size_t)h->nbox, s));
+        continue;
       }
+      rg.in[ng] = h->ws<T>(c.nX + g);
+      rg.out[ng] = out;
+      rg.g_io[ng] = ng;
+      rg.g_begin[ng] = ng;
+      rg.term_io[ng] = ng;
+      rg.term_m[ng] = h->zreg_row[g];
+      ++ng;
     }
-    rg.g_begin[c.nY] = nt;
-    RK_TRY(run_merge<T>(h, 2, rg, s));
+    rg.n_groups = ng;
+    rg.g_begin[ng] = ng;
+    if (ng > 0) RK_TRY(run_split<T>(h, 2, rg, s, nullptr, RK_PROF_Z_MERGE));
     {
       ProfScope ps(h, prof_cls<T>(RK_PROF_Z_STIFF), s);
       cudaError_t e = launch_zcorr<T>(zcorr_args<T>(h), s);

@@ -10,7 +10,7 @@
 // and c_p = 0 for the other p.  Writing g_p = c_p D_p + delta_p at every node, the
 // part c_p D_p is a convolution of E_g(p) with T * Tbar scaled by c_p: one spectral
 // multiplier c_p n |T^_{alpha_z}|^2 per group, applied by a z pass with one forward
-// and one inverse transform per group (rk_passes.cuh, merge kernel).  delta_p is
+// and one inverse transform per group (rk_passes.cuh, split kernel).  delta_p is
 // zero at regular nodes and at nodes farther than the support from chi (where D
 // vanishes), so it lives on the boundary layers; this file adds its reflected
 // convolution to G by direct sums over the short z-windows around those nodes:
