@@ -136,7 +136,19 @@ cudaError_t merge_n(int axis, const PassArgs<T>& a, cudaStream_t s, const TileMa
     const long long npairs = ((long long)a.ny * a.nz + 1) / 2;  // an odd last row pairs with zeros
     const unsigned nb = (unsigned)((npairs + LX - 1) / LX);
     auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) % 16) == 0; };
-    if (X::MERGE_BULK && a.cg_p && a.n_groups == 1 && aligned(a.cg_p) && (!a.out_mask || aligned(a.out_mask))) {
+    const bool fed = X::MERGE_BULK && a.cg_p && a.out_mask && a.n_groups == 1 && aligned(a.cg_p) && aligned(a.out_mask);
+    if constexpr (sizeof(T) == 4 && X::FIVE && X::SMEM >= X::TILE) {
+      if (fed && a.g_begin[1] - a.g_begin[0] == 2 && aligned(a.in[a.term_io[a.g_begin[0]]]) &&
+          aligned(a.in[a.term_io[a.g_begin[0] + 1]])) {
+        auto k = k_x_merge_fed2<T, N, LX>;
+        cudaError_t e = set_smem(k, X::SMEM_MERGE_FEED);
+        if (e != cudaSuccess) return e;
+        count_launch();
+        k<<<nb, X::THREADS, X::SMEM_MERGE_FEED, s>>>(a);
+        return cudaGetLastError();
+      }
+    }
+    if (fed) {
       auto k = k_x_merge<T, N, LX, true>;
       cudaError_t e = set_smem(k, X::SMEM_MERGE_FEED);
       if (e != cudaSuccess) return e;

@@ -535,6 +535,54 @@ __device__ __forceinline__ void cg_pap_reduce(double v, const PassArgs<T>& a) {
   }
 }
 
+// The same reduction with warp shuffles for blocks of whole warps (fixed order as
+// well: lanes in a butterfly, warps in index order, the partials in block order).
+template <int THREADS, typename T>
+__device__ __forceinline__ void cg_pap_reduce_warps(double v, const PassArgs<T>& a) {
+  static_assert(THREADS % 32 == 0, "whole warps");
+  constexpr int W = THREADS / 32;
+  __shared__ double wsum[W];
+  __shared__ bool last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) s += wsum[w];
+    a.partials[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += THREADS) s += ((volatile double*)a.partials)[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double pap = 0.0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) pap += wsum[w];
+    CGState* st = a.cg;
+    st->pAp = pap;
+    double al = 0.0;
+    if (st->rz > 0.0) {
+      if (pap > 0.0 && isfinite(pap))
+        al = st->rz / pap;
+      else
+        st->flag = 1;
+    }
+    st->alpha = al;
+    *a.counter = 0u;
+  }
+}
+
 // FEED: the rows of r and p arrive by bulk async copies (the CG variant); a
 // separate instantiation, so that the plain variant keeps the default shared
 // memory carve-out (its twiddle and multiplier loads live in L1).
@@ -673,8 +721,9 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
   }
 }
 
-// FEED: the CG variant (one group, p . Ap epilogue) with the block's rows of p and
-// of the output mask arriving by bulk async copies while the block transforms.
+// FEED: the CG variant (one group, an output mask, p . Ap epilogue) with the
+// block's rows of p and of the mask arriving by bulk async copies while the block
+// transforms.
 template <typename T, int N, int LX, bool FEED>
 __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN_BLOCKS_MERGE)
     k_x_merge(const PassArgs<T> a) {
@@ -705,12 +754,12 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
     if (threadIdx.x < 32) {
       if (threadIdx.x == 0) {
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar, (uint32_t)(rows * N * sizeof(T) + (a.out_mask ? rows * N : 0)));
+        mbar_arrive_expect_tx(&bar, (uint32_t)(rows * N * sizeof(T) + rows * N));
       }
       __syncwarp();
       for (int j = threadIdx.x; j < rows; j += 32)
         bulk_g2s(ptile + j * X::PITCH, a.cg_p + (row0 + j) * N, (uint32_t)(N * sizeof(T)), &bar);
-      if (threadIdx.x == 0 && a.out_mask) bulk_g2s(mtile, a.out_mask + row0 * N, (uint32_t)(rows * N), &bar);
+      if (threadIdx.x == 0) bulk_g2s(mtile, a.out_mask + row0 * N, (uint32_t)(rows * N), &bar);
     }
 #pragma unroll
     for (int r = 0; r < X::R; ++r) acc[r] = cmk((T)0, (T)0);
@@ -727,37 +776,42 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
       for (int r = 0; r < X::R; ++r) acc[r] = acc[r] + spec_mul(v[r], a.coef, N, m, F::spec_idx(t, r), a.reflect);
     }
     F::inverse(acc, t, buf, a.tw);
-    // the tiles: bounded wait; on a time-out the block records it, waits (bounded)
-    // for the copies still in flight and writes nothing, but still takes part in
-    // the p . Ap reduction (with 0), so that its counter ends the launch reset
-    const bool got = mbar_wait(&bar, 0u, a.short_wait ? 0u : kWaitLimit);
-    if (__syncthreads_or(!got)) {
-      if (threadIdx.x == 0) flag_wait_error(a.err);
+    // the tiles: bounded wait; a thread whose wait runs out records it and waits
+    // (bounded) for the copies still in flight.  The block then completes as usual
+    // (its output is invalid and the call reports the time-out), so that it still
+    // takes part in the p . Ap reduction and the counter ends the launch reset.
+    if (!mbar_wait(&bar, 0u, a.short_wait ? 0u : kWaitLimit)) {
+      flag_wait_error(a.err);
       mbar_wait(&bar, 0u);
-      cg_pap_reduce<X::THREADS>(0.0, a);
-      return;
     }
-    if (a.out_mask) {
-      const uint8_t* mk = mtile + (2 * l) * N;
+    // (rows past the end of the box: their mask bytes are not loaded, and neither
+    // their outputs nor their p . Ap terms are used)
+    const uint8_t* mk = mtile + (2 * l) * N;
 #pragma unroll
-      for (int r = 0; r < X::R; ++r) {
-        const int xp = F::nat_pos(t, r);
-        acc[r] = pmul(acc[r], cmk((T)mk[xp], ok1 ? (T)mk[N + xp] : (T)0));
-      }
+    for (int r = 0; r < X::R; ++r) {
+      const int xp = F::nat_pos(t, r);
+      acc[r] = pmul(acc[r], cmk((T)mk[xp], (T)mk[N + xp]));
     }
     T* out = a.out[a.g_io[0]];
-    DotAccPair<T> dot;
-    if (ok) {
-      const T* pa = ptile + (2 * l) * X::PITCH;
+    if (ok)
 #pragma unroll
       for (int r = 0; r < X::R; ++r) {
         const int xp = F::nat_pos(t, r);
         out[r0 + xp] = acc[r].x;
         if (ok1) out[r1 + xp] = acc[r].y;
+      }
+    DotAccPair<T> dot;
+    const T* pa = ptile + (2 * l) * X::PITCH;
+    if (ok)
+#pragma unroll
+      for (int r = 0; r < X::R; ++r) {
+        const int xp = F::nat_pos(t, r);
         dot.add(cmk(pa[xp], ok1 ? pa[X::PITCH + xp] : (T)0), acc[r]);
       }
-    }
-    cg_pap_reduce<X::THREADS>(dot.value(), a);
+    if constexpr (X::THREADS % 32 == 0)
+      cg_pap_reduce_warps<X::THREADS>(dot.value(), a);
+    else
+      cg_pap_reduce<X::THREADS>(dot.value(), a);
     return;
   }
   for (int g = 0; g < a.n_groups; ++g) {
@@ -813,6 +867,130 @@ __global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, XPass<T, N, LX>::MIN
       cg_pap_reduce<X::THREADS>(dot.value(), a);
     }
   }
+}
+
+// The CG x merge of two terms (the linear basis) with every row it reads arriving
+// by bulk async copies: the first input into the transpose buffer (read before the
+// first transform writes it), the second into a row tile, and p and the output
+// mask into that tile once the second input has been read, while the block
+// transforms.  Four blocks per SM (128 registers): at N = 256, 74.3 us against
+// 75-83 us for the variant that loads the inputs with per-thread loads.
+template <typename T, int N, int LX>
+__global__ void __launch_bounds__(XPass<T, N, LX>::THREADS, 4) k_x_merge_fed2(const PassArgs<T> a) {
+  using X = XPass<T, N, LX>;
+  using F = typename X::F;
+  static_assert(X::SMEM >= X::TILE, "the first input tile lives in the transpose buffer");
+  RK_DYN_SMEM(unsigned char, smem);
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem);
+  T* tileA = reinterpret_cast<T*>(smem);
+  T* tileB = reinterpret_cast<T*>(smem + X::SMEM);
+  uint8_t* mtile = smem + X::SMEM + X::TILE;
+  __shared__ uint64_t bar[3];
+  const int t = threadIdx.x % X::P, l = threadIdx.x / X::P;
+  const long long q = (long long)blockIdx.x * LX + l;
+  const long long nrows_all = (long long)a.ny * a.nz;
+  const long long npairs = (nrows_all + 1) / 2;  // an odd last row pairs with a row of zeros
+  const bool ok = q < npairs;
+  const bool ok1 = 2 * q + 1 < nrows_all;
+  const long long r0 = 2 * q * a.nx, r1 = r0 + a.nx;
+  const long long row0 = 2LL * blockIdx.x * LX;
+  const int rows = (int)((nrows_all - row0) < X::ROWS ? (nrows_all - row0) : X::ROWS);
+  typename X::B buf{sm + (size_t)l * X::B::SIZE};
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
+    mbar_init_fence();
+  }
+  RK_SYNC();
+  const int q0 = a.g_begin[0];
+  const T* in0 = a.in[a.term_io[q0]];
+  const T* in1 = a.in[a.term_io[q0 + 1]];
+  const uint32_t row_bytes = (uint32_t)(N * sizeof(T));
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar[0], (uint32_t)rows * row_bytes);
+      mbar_arrive_expect_tx(&bar[1], (uint32_t)rows * row_bytes);
+    }
+    __syncwarp();
+    for (int j = threadIdx.x; j < rows; j += 32) bulk_g2s(tileA + j * X::PITCH, in0 + (row0 + j) * N, row_bytes, &bar[0]);
+    for (int j = threadIdx.x; j < rows; j += 32) bulk_g2s(tileB + j * X::PITCH, in1 + (row0 + j) * N, row_bytes, &bar[1]);
+  }
+  // bounded waits: a thread whose wait runs out records it and waits (bounded) for
+  // the copy still in flight; the block then completes as usual (its output is
+  // invalid and the call reports the time-out) and takes part in the reduction
+  auto wait = [&](int k, bool first) {
+    if (!mbar_wait(&bar[k], 0u, (first && a.short_wait) ? 0u : kWaitLimit)) {
+      flag_wait_error(a.err);
+      mbar_wait(&bar[k], 0u);
+    }
+  };
+  cpx<T> v[X::R], acc[X::R];
+  wait(0, true);
+  {
+    const T* ta = tileA + (2 * l) * X::PITCH;
+#pragma unroll
+    for (int r = 0; r < X::R; ++r) {
+      const int xp = F::nat_pos(t, r);
+      v[r] = cmk(ok ? ta[xp] : (T)0, ok1 ? ta[X::PITCH + xp] : (T)0);
+    }
+  }
+  F::forward(v, t, buf, a.tw);
+#pragma unroll
+  for (int r = 0; r < X::R; ++r) acc[r] = spec_mul(v[r], a.coef, N, a.term_m[q0], F::spec_idx(t, r), a.reflect);
+  wait(1, false);
+  {
+    const T* tb = tileB + (2 * l) * X::PITCH;
+#pragma unroll
+    for (int r = 0; r < X::R; ++r) {
+      const int xp = F::nat_pos(t, r);
+      v[r] = cmk(ok ? tb[xp] : (T)0, ok1 ? tb[X::PITCH + xp] : (T)0);
+    }
+  }
+  RK_SYNC();  // the second input is in registers: p and the mask may land in its tile
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar[2], (uint32_t)rows * row_bytes + (uint32_t)(rows * N));
+    }
+    __syncwarp();
+    for (int j = threadIdx.x; j < rows; j += 32) bulk_g2s(tileB + j * X::PITCH, a.cg_p + (row0 + j) * N, row_bytes, &bar[2]);
+    if (threadIdx.x == 0) bulk_g2s(mtile, a.out_mask + row0 * N, (uint32_t)(rows * N), &bar[2]);
+  }
+  F::forward(v, t, buf, a.tw);
+#pragma unroll
+  for (int r = 0; r < X::R; ++r) acc[r] = acc[r] + spec_mul(v[r], a.coef, N, a.term_m[q0 + 1], F::spec_idx(t, r), a.reflect);
+  F::inverse(acc, t, buf, a.tw);
+  wait(2, false);
+  // (rows past the end of the box: their mask bytes are not loaded, and neither
+  // their outputs nor their p . Ap terms are used)
+  const uint8_t* mk = mtile + (2 * l) * N;
+#pragma unroll
+  for (int r = 0; r < X::R; ++r) {
+    const int xp = F::nat_pos(t, r);
+    acc[r] = pmul(acc[r], cmk((T)mk[xp], (T)mk[N + xp]));
+  }
+  T* out = a.out[a.g_io[0]];
+  if (ok)
+#pragma unroll
+    for (int r = 0; r < X::R; ++r) {
+      const int xp = F::nat_pos(t, r);
+      out[r0 + xp] = acc[r].x;
+      if (ok1) out[r1 + xp] = acc[r].y;
+    }
+  DotAccPair<T> dot;
+  const T* pa = tileB + (2 * l) * X::PITCH;
+  if (ok)
+#pragma unroll
+    for (int r = 0; r < X::R; ++r) {
+      const int xp = F::nat_pos(t, r);
+      dot.add(cmk(pa[xp], ok1 ? pa[X::PITCH + xp] : (T)0), acc[r]);
+    }
+  if constexpr (X::THREADS % 32 == 0)
+    cg_pap_reduce_warps<X::THREADS>(dot.value(), a);
+  else
+    cg_pap_reduce<X::THREADS>(dot.value(), a);
 }
 
 // ------------------------------------------------------- fused z pass (Alg. 2-4)
