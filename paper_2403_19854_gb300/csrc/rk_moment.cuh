@@ -12,32 +12,41 @@ namespace rk {
 // solves, then b^0 = row 1, b^k = -(1/a_k) row (1+k) (Eq. 83-85, scaled basis;
 // b^z = 0 in 2D).
 // A pivot <= 1e-14 * trace(M) marks the node singular: its b are set to 0 and the
-// node is counted.
+// node is counted.  The basis size S is a template parameter, so that the loops
+// unroll and the packed factor stays in registers (with a run-time size it lived
+// in local memory).
+template <int S>
 __global__ void __launch_bounds__(128) k_moment_solve(const MomentArgs a) {
-  const int s = a.s;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.nbox;
        i += (long long)gridDim.x * blockDim.x) {
-    double L[kMaxS * (kMaxS + 1) / 2];  // packed lower triangle, row-major
+    double L[S * (S + 1) / 2];  // packed lower triangle, row-major
     const bool in = a.chi[i] != 0;
     double tr = 0.0;
-    for (int p = 0; p < s; ++p)
+#pragma unroll
+    for (int p = 0; p < S; ++p)
+#pragma unroll
       for (int q = 0; q <= p; ++q) {
         double v = in ? a.mom[(long long)a.pq[p][q] * a.nbox + i] : (p == q ? 1.0 : 0.0);
         L[p * (p + 1) / 2 + q] = v;
         if (p == q) tr += fabs(v);
       }
     bool bad = false;
-    for (int j = 0; j < s && !bad; ++j) {
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (bad) continue;
       double d = L[j * (j + 1) / 2 + j];
+#pragma unroll
       for (int k = 0; k < j; ++k) d -= L[j * (j + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
       if (!(d > 1e-14 * tr)) {
         bad = true;
-        break;
+        continue;
       }
       const double l = sqrt(d);
       L[j * (j + 1) / 2 + j] = l;
-      for (int r = j + 1; r < s; ++r) {
+#pragma unroll
+      for (int r = j + 1; r < S; ++r) {
         double v = L[r * (r + 1) / 2 + j];
+#pragma unroll
         for (int k = 0; k < j; ++k) v -= L[r * (r + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
         L[r * (r + 1) / 2 + j] = v / l;
       }
@@ -46,27 +55,35 @@ __global__ void __launch_bounds__(128) k_moment_solve(const MomentArgs a) {
       atomicAdd(a.n_singular, 1ull);
       atomicMin(a.first_singular, (unsigned long long)i);
     }
+#pragma unroll
     for (int row = 0; row < 4; ++row) {
-      double x[kMaxS];
-      for (int p = 0; p < s; ++p) x[p] = (p == row) ? 1.0 : 0.0;
+      double x[S];
+#pragma unroll
+      for (int p = 0; p < S; ++p) x[p] = (p == row) ? 1.0 : 0.0;
       if (!bad && row <= a.dim) {  // b^k = 0 on an absent axis
-        for (int p = 0; p < s; ++p) {
+#pragma unroll
+        for (int p = 0; p < S; ++p) {
           double v = x[p];
+#pragma unroll
           for (int k = 0; k < p; ++k) v -= L[p * (p + 1) / 2 + k] * x[k];
           x[p] = v / L[p * (p + 1) / 2 + p];
         }
-        for (int p = s - 1; p >= 0; --p) {
+#pragma unroll
+        for (int p = S - 1; p >= 0; --p) {
           double v = x[p];
-          for (int k = p + 1; k < s; ++k) v -= L[k * (k + 1) / 2 + p] * x[k];
+#pragma unroll
+          for (int k = p + 1; k < S; ++k) v -= L[k * (k + 1) / 2 + p] * x[k];
           x[p] = v / L[p * (p + 1) / 2 + p];
         }
       } else {
-        for (int p = 0; p < s; ++p) x[p] = 0.0;
+#pragma unroll
+        for (int p = 0; p < S; ++p) x[p] = 0.0;
       }
       const double sc = row == 0 ? 1.0 : -a.inv_a[row - 1];
-      for (int p = 0; p < s; ++p) {
+#pragma unroll
+      for (int p = 0; p < S; ++p) {
         const double v = sc * x[p];
-        const long long o = ((long long)row * s + p) * a.nbox + i;
+        const long long o = ((long long)row * S + p) * a.nbox + i;
         a.b64[o] = v;
         if (a.b32) a.b32[o] = (float)v;
       }

@@ -20,8 +20,14 @@ bool supported_length(int n) {
 cudaError_t launch_moment_solve(const MomentArgs& a, cudaStream_t s) {
   const long long nb = (a.nbox + 127) / 128;
   const unsigned grid = (unsigned)(nb < 152 * 64 ? nb : 152 * 64);
-  count_launch();
-  k_moment_solve<<<grid, 128, 0, s>>>(a);
+  switch (a.s) {  // the basis sizes of degree 1 and 2 in 1D, 2D and 3D
+    case 2: count_launch(); k_moment_solve<2><<<grid, 128, 0, s>>>(a); break;
+    case 3: count_launch(); k_moment_solve<3><<<grid, 128, 0, s>>>(a); break;
+    case 4: count_launch(); k_moment_solve<4><<<grid, 128, 0, s>>>(a); break;
+    case 6: count_launch(); k_moment_solve<6><<<grid, 128, 0, s>>>(a); break;
+    case 10: count_launch(); k_moment_solve<10><<<grid, 128, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
