@@ -846,32 +846,6 @@ void axis_tables(int n, double a_tilde, int reach, int mmax, std::vector<double>
   for (int m = 0; m < n; ++m) tw[m] = cmk(trig::cos2pi(m, n), -trig::sin2pi(m, n));
 }
 
-// Eq. 66 in discrete form: along each axis the projection of chi must leave a
-// circular run of at least `reach` empty node indices, so no two nodes of Omega
-// are within the support through the periodic boundary.
-bool gap_ok(const std::vector<uint8_t>& chi, const int n[3], int reach, int dim) {
-  for (int ax = 0; ax < dim; ++ax) {
-    std::vector<uint8_t> occ(n[ax], 0);
-    for (int k = 0; k < n[2]; ++k)
-      for (int j = 0; j < n[1]; ++j)
-        for (int i = 0; i < n[0]; ++i)
-          if (chi[(size_t)i + (size_t)n[0] * ((size_t)j + (size_t)n[1] * k)]) occ[ax == 0 ? i : (ax == 1 ? j : k)] = 1;
-    int best = 0, run = 0;
-    bool any = false;
-    for (int t = 0; t < 2 * n[ax]; ++t) {
-      if (occ[t % n[ax]]) {
-        any = true;
-        run = 0;
-      } else {
-        run = std::min(run + 1, n[ax]);
-        best = std::max(best, run);
-      }
-    }
-    if (any && best < reach) return false;
-  }
-  return true;
-}
-
 template <typename T>
 void to_device_async(T* dst, const std::vector<T>& src, cudaStream_t s) {
   cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
@@ -2294,25 +2268,26 @@ rk_status rk_setup(const rk_grid* grid, const uint8_t* chi, const uint8_t* chi_g
       (st = h->alloc(&h->ws32, (size_t)ws_fields(h->chain) * n)) || (st = h->alloc(&h->counters, 2)))
     return bail(st);
   if ((st = setup_tma(h)) != RK_OK) return bail(st);
-  std::vector<uint8_t> hchi(n), hgam(n, 0), homg(n);
-  cudaError_t e = cudaMemcpy(hchi.data(), chi, n, cudaMemcpyDefault);
-  if (e == cudaSuccess && chi_gamma) e = cudaMemcpy(hgam.data(), chi_gamma, n, cudaMemcpyDefault);
-  if (e == cudaSuccess) e = cudaMemcpy(h->V, V, n * sizeof(double), cudaMemcpyDefault);
+  // inputs to the device; the masks are made 0/1, Omega counted and the gap of
+  // Eq. 66 checked on the device, with one small read-back
+  uint8_t* scr = nullptr;
+  if ((st = h->alloc(&scr, (size_t)16 + h->n[0] + h->n[1] + h->n[2])) != RK_OK) return bail(st);
+  cudaError_t e = cudaMemcpyAsync(h->chi, chi, n, cudaMemcpyDefault, s);
+  if (e == cudaSuccess)
+    e = chi_gamma ? cudaMemcpyAsync(h->chi_gamma, chi_gamma, n, cudaMemcpyDefault, s) : cudaMemsetAsync(h->chi_gamma, 0, n, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->V, V, n * sizeof(double), cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = launch_setup_masks(h->chi, h->chi_gamma, h->chi_omega, h->n, dim, reach, scr, s);
+  unsigned char res[12];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(res, scr, sizeof(res), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return bail(cuda_fail(e, "copy inputs"));
-  long long nom = 0;
-  for (long long i = 0; i < n; ++i) {
-    hchi[i] = hchi[i] ? 1 : 0;
-    hgam[i] = (hgam[i] && hchi[i]) ? 1 : 0;
-    homg[i] = hchi[i] & (uint8_t)(1 - hgam[i]);
-    nom += hchi[i];
-  }
-  h->n_omega = nom;
-  if (!gap_ok(hchi, h->n, reach, dim))
+  unsigned long long nom = 0;
+  int gap_narrow = 0;
+  memcpy(&nom, res, sizeof(nom));
+  memcpy(&gap_narrow, res + 8, sizeof(gap_narrow));
+  h->n_omega = (long long)nom;
+  if (gap_narrow)
     return bail(fail(RK_ERR_UNSUPPORTED, "gap between the domain and its periodic image is narrower than the support (Eq. 66)"));
-  e = cudaMemcpy(h->chi, hchi.data(), n, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->chi_gamma, hgam.data(), n, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->chi_omega, homg.data(), n, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return bail(cuda_fail(e, "copy masks"));
 
   // per-axis tables for m in [0, 2 deg] (moments need 2 deg; the chains use <= deg)
   const int mmax = 2 * degree;

@@ -55,6 +55,12 @@ struct MomentArgs {
   unsigned long long* first_singular;
 };
 cudaError_t launch_moment_solve(const MomentArgs& a, cudaStream_t s);
+// set-up of the masks: chi and chi_gamma to 0/1 in place, chi_omega, the count of
+// chi nodes (scratch bytes 0..7) and the Eq. 66 gap check (bytes 8..11: 1 when the
+// gap along one of the dim axes is narrower than reach); scratch holds
+// 16 + n0 + n1 + n2 bytes and is cleared by the call
+cudaError_t launch_setup_masks(uint8_t* chi, uint8_t* gam, uint8_t* omg, const int n[3], int dim, int reach,
+                               uint8_t* scratch, cudaStream_t s);
 
 // ------------------------------------------------- coefficient compression
 // out = 1 where every node within +-r along `axis` (periodic) has in = 1.

@@ -31,6 +31,76 @@ cudaError_t launch_moment_solve(const MomentArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------- set-up: masks and the Eq. 66 gap
+// chi and chi_gamma to 0/1 in place (chi_gamma restricted to chi), chi_omega = chi
+// and not chi_gamma, the count of chi nodes (scratch[0..7]) and the occupied
+// indices of each axis (scratch[16 + i], [16 + n0 + j], [16 + n0 + n1 + k]); each
+// block gathers its occupied indices in shared memory first.
+__global__ void k_setup_masks(uint8_t* chi, uint8_t* gam, uint8_t* omg, int n0, int n1, int n2, long long n,
+                              uint8_t* scratch) {
+  extern __shared__ uint8_t occ[];
+  const int np = n0 + n1 + n2;
+  for (int t = threadIdx.x; t < np; t += blockDim.x) occ[t] = 0;
+  __syncthreads();
+  unsigned cnt = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint8_t x = chi[i] ? 1 : 0;
+    const uint8_t g = (gam[i] && x) ? 1 : 0;
+    chi[i] = x;
+    gam[i] = g;
+    omg[i] = x & (uint8_t)(1 - g);
+    if (x) {
+      ++cnt;
+      const long long jk = i / n0;
+      occ[i - jk * n0] = 1;
+      occ[n0 + (int)(jk % n1)] = 1;
+      occ[n0 + n1 + (int)(jk / n1)] = 1;
+    }
+  }
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(reinterpret_cast<unsigned long long*>(scratch), (unsigned long long)cnt);
+  __syncthreads();
+  for (int t = threadIdx.x; t < np; t += blockDim.x)
+    if (occ[t]) scratch[16 + t] = 1;
+}
+
+// Eq. 66 in discrete form: along each axis of the problem the occupied indices must
+// leave a circular run of at least `reach` empty ones, so that no two nodes of
+// Omega are within the support through the periodic boundary; scratch[8..11] = 1
+// if not.
+__global__ void k_setup_gap(uint8_t* scratch, int n0, int n1, int n2, int dim, int reach) {
+  const int ax = threadIdx.x;
+  if (ax >= dim) return;
+  const int n = ax == 0 ? n0 : (ax == 1 ? n1 : n2);
+  const uint8_t* o = scratch + 16 + (ax == 0 ? 0 : (ax == 1 ? n0 : n0 + n1));
+  int best = 0, run = 0;
+  bool any = false;
+  for (int t = 0; t < 2 * n; ++t) {
+    if (o[t % n]) {
+      any = true;
+      run = 0;
+    } else {
+      run = min(run + 1, n);
+      best = max(best, run);
+    }
+  }
+  if (any && best < reach) *reinterpret_cast<int*>(scratch + 8) = 1;
+}
+
+cudaError_t launch_setup_masks(uint8_t* chi, uint8_t* gam, uint8_t* omg, const int n[3], int dim, int reach,
+                               uint8_t* scratch, cudaStream_t s) {
+  const long long nbox = (long long)n[0] * n[1] * n[2];
+  const int np = n[0] + n[1] + n[2];
+  cudaError_t e = cudaMemsetAsync(scratch, 0, (size_t)16 + np, s);
+  if (e != cudaSuccess) return e;
+  const long long nb = (nbox + 255) / 256;
+  count_launch();
+  k_setup_masks<<<(unsigned)(nb < 152 * 8 ? nb : 152 * 8), 256, np, s>>>(chi, gam, omg, n[0], n[1], n[2], nbox, scratch);
+  count_launch();
+  k_setup_gap<<<1, 32, 0, s>>>(scratch, n[0], n[1], n[2], dim, reach);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------- coefficient compression
 __global__ void k_erode(uint8_t* out, const uint8_t* in, int axis, int r, int nx, int ny, int nz) {
   const long long n = (long long)nx * ny * nz;
