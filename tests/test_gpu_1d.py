@@ -119,3 +119,17 @@ def test_1d_rejects_the_spectral_preconditioner():
     with pytest.raises(rk.RKError):
         H.apply_precond(tdev(W.random_field(p.nbox, 1)))
     H.close()
+
+
+def test_1d_gap_narrower_than_support_is_rejected():
+    """Eq. 66 on a line: with a = 2h the reach is one node, so a domain that fills
+    every node of the line touches its periodic image and the set-up refuses it."""
+    p = W.line_problem(16, 2.0, 1)
+    chi = p.chi.copy()
+    chi[14] = 1
+    chi[15] = 1
+    with pytest.raises(rk.RKError) as e:
+        rk.Handle(p.n, p.h, tdev(chi), tdev(p.chi_gamma), tdev(p.V), 1, 2.0)
+    assert e.value.status == 8
+    H = rk.Handle(p.n, p.h, tdev(p.chi), tdev(p.chi_gamma), tdev(p.V), 1, 2.0)
+    H.close()

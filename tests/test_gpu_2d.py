@@ -102,3 +102,23 @@ def test_2d_rejects_the_spectral_preconditioner():
     with pytest.raises(rk.RKError):
         H.apply_precond(tdev(W.random_field(p.nbox, 1)))
     H.close()
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_2d_gap_narrower_than_support_is_rejected(axis):
+    """Eq. 66 on a plane: with a = 2h the reach is one node, so a domain that fills
+    every index of x (or of y) touches its periodic image and the set-up refuses it;
+    the single z index, which every node occupies, is not an axis of the problem."""
+    p = W.plane_problem(16, 2.0, 1)
+    chi = p.chi.reshape(16, 16).copy()          # [y, x]
+    if axis == 0:
+        chi[:, 14] = chi[:, 0]
+        chi[:, 15] = chi[:, 0]
+    else:
+        chi[14, :] = chi[0, :]
+        chi[15, :] = chi[0, :]
+    with pytest.raises(rk.RKError) as e:
+        rk.Handle(p.n, p.h, tdev(chi.reshape(-1)), tdev(p.chi_gamma), tdev(p.V), 1, 2.0)
+    assert e.value.status == 8
+    H = rk.Handle(p.n, p.h, tdev(p.chi), tdev(p.chi_gamma), tdev(p.V), 1, 2.0)   # the gap kept: accepted
+    H.close()
