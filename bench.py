@@ -236,6 +236,35 @@ def run_ku(args):
     return 0
 
 
+def run_cg(args):
+    """A short mixed CG solve alone, for external profilers: set-up as run_ku (the
+    cube domain of the smallest side in the --box), then --reps iterations of the
+    FP32 CG with its fused x passes (Alg. 5; the iteration cap ends it).  Prints the
+    iterations and the device memory held."""
+    import torch
+    from paper_2403_19854_gb300 import rk
+    from paper_2403_19854_gb300 import workloads as W
+    box = tuple(int(v) for v in args.box.split("x"))
+    if len(box) == 1:
+        box = box * 3
+    at = 2.5 if args.degree == 1 else 3.0
+    p = W.cube_problem(min(box), at, args.degree, "sin")
+    if box != p.n:
+        p = W.embed(p, box)
+    dev = torch.device("cuda:0")
+    H = rk.Handle.from_problem(p, device=dev)
+    r = torch.as_tensor(p.r, device=dev)
+    g = torch.as_tensor(p.g, device=dev)
+    _, _, info = H.solve(r, g, opts=rk.default_opts(precision="mixed", tol=1e-10, max_iter=args.reps),
+                         raise_on_error=False)
+    torch.cuda.synchronize()
+    free, total = torch.cuda.mem_get_info()
+    print(f"box {box} degree {args.degree}: mixed CG, {info['iterations']} iterations (status {info['status']}), "
+          f"device memory {total - free:.3e} B in use")
+    H.close()
+    return 0
+
+
 # ------------------------------------------------------------- our arm
 # Algorithmic bytes per box node of one launch of each kernel class inside the CG
 # iteration (linear basis s = 4, w = bytes per real, u8 masks, int32 node index):
@@ -764,13 +793,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=0.0,
                     help="ncu dram bytes per launch of the dominant kernel (from profiles/), if measured")
-    ap.add_argument("--workload", default="cube", choices=["cube", "batched", "ku"],
+    ap.add_argument("--workload", default="cube", choices=["cube", "batched", "ku", "cg"],
                     help="cube: the 256^3 cube solve (default); batched: uneven embedded domains; "
-                         "ku: set-up and --reps K.u on --box (for external profilers)")
-    ap.add_argument("--box", default="128", help="ku: box sides, n or a x b x c")
+                         "ku: set-up and --reps K.u on --box (for external profilers); "
+                         "cg: set-up and --reps mixed CG iterations on --box (for external profilers)")
+    ap.add_argument("--box", default="128", help="ku, cg: box sides, n or a x b x c")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="ku: precision of K.u")
     ap.add_argument("--degree", type=int, default=1, choices=[1, 2], help="ku: basis degree")
-    ap.add_argument("--reps", type=int, default=4, help="ku: number of K.u")
+    ap.add_argument("--reps", type=int, default=4, help="ku: number of K.u; cg: iteration cap")
     ap.add_argument("--domains", type=int, default=64, help="batched: number of domains")
     ap.add_argument("--spheres-solve", type=int, default=1,
                     help="time the 12-spheres quadratic solves (mixed and FP64 PCG to 1e-2; about 45 s)")
@@ -783,6 +813,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "cg":
+        return run_cg(args)
     if args.workload == "ku":
         return run_ku(args)
     return run_ours(args)
