@@ -50,11 +50,12 @@ typedef enum rk_status {
   RK_ERR_SINGULAR_MOMENT = 4,  /* M(x) not positive definite at some node of Omega */
   RK_ERR_NOT_CONVERGED = 5,    /* iteration cap reached before the tolerance */
   RK_ERR_BREAKDOWN = 6,        /* CG breakdown: p^T A p <= 0 or not finite */
-  RK_ERR_TIMEOUT = 7,          /* a bounded device-side wait ran out: a y/z pass waited
-                                  too long for an input tile (TMA); the kernel gave up
-                                  and the result is invalid.  Reported by the next call
-                                  of the handle that synchronises (solves, calls with
-                                  host arrays). */
+  RK_ERR_TIMEOUT = 7,          /* a bounded device-side wait ran out: a pass waited too
+                                  long for an input tile (the TMA tiles of the y/z
+                                  passes, the bulk row copies of the x passes inside
+                                  CG); the kernel gave up and the result is invalid.
+                                  Reported by the next call of the handle that
+                                  synchronises (solves, calls with host arrays). */
   RK_ERR_UNSUPPORTED = 8       /* grid size not built, gap too narrow, odd n[0] ... */
 } rk_status;
 
@@ -373,10 +374,11 @@ const char* rk_profile_class_name(int32_t cls);
 /*
  * rk_debug_short_waits -- a diagnostic switch for tests of the time-out path (the
  * paper has no counterpart).  While enable = 1, the first bounded wait of every
- * block of this handle's TMA-fed passes for an input tile gives up at once: the
- * block records the time-out in the handle's error word, still waits (with the
- * normal limit) for its copy in flight to land, and returns without writing its
- * outputs.  The next call of the handle that synchronises (a solve, or a call on
+ * block of this handle's TMA- or bulk-copy-fed passes for an input tile gives up at
+ * once: the block records the time-out in the handle's error word, still waits
+ * (with the normal limit) for its copy in flight to land, and returns without
+ * writing its outputs (the x merge of a CG step instead completes, its outputs
+ * invalid, so that its p . Ap reduction ends).  The next call of the handle that synchronises (a solve, or a call on
  * host arrays) then returns RK_ERR_TIMEOUT and clears the word; results computed
  * meanwhile are invalid.  enable = 0 restores the normal waits of 2^26 polls.
  * Passes fed by cp.async copies (boxes whose rows are not a multiple of 16 bytes)
