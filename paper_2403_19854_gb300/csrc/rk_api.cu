@@ -942,7 +942,7 @@ rk_status read_scalar(rk_handle* h, const double* dptr, double* out, cudaStream_
 
 rk_status norm2(rk_handle* h, const double* v, double* out, cudaStream_t s) {
   RK_CK(launch_dot<double, double>(v, v, h->nbox, h->partials, h->dscal, s));
-  double r2;
+  double r2 = 0.0;
   RK_TRY(read_scalar(h, h->dscal, &r2, s));
   RK_TRY(check_device_flag(h));
   *out = std::sqrt(std::max(r2, 0.0));
@@ -1349,7 +1349,7 @@ rk_status solve_masked(rk_handle* h, const double* F, double* x, const rk_solve_
   double* r64 = h->v64(1);
   double* p64 = h->v64(2);
   double* Ap64 = h->v64(3);
-  double fn;
+  double fn = 0.0;
   RK_TRY(norm2(h, F, &fn, s));
   info->f_norm = fn;
   if (!std::isfinite(fn))
@@ -1551,7 +1551,7 @@ rk_status transient_implicit(rk_handle* h, const double* f, const double* g, dou
     RK_CK(launch_axpby(b, dt, f, 1.0, n, s));
     RK_CK(launch_axpby(b, -dt, KdG, 1.0, n, s));
     RK_CK(launch_mask(b, b, h->chi_omega, n, s));
-    double bn;
+    double bn = 0.0;
     RK_TRY(dot(b, b, &bn));
     bn = std::sqrt(bn);
     if (bn == 0.0) {
@@ -1561,18 +1561,18 @@ rk_status transient_implicit(rk_handle* h, const double* f, const double* g, dou
     RK_TRY(apply_A(x, Ap));
     RK_CK(launch_sub(r, b, Ap, n, s));
     RK_CK(launch_copy<double>(p, r, n, s));
-    double rr;
+    double rr = 0.0;
     RK_TRY(dot(r, r, &rr));
     int it = 0;
     while (std::sqrt(rr) > o.tol * bn && it < o.max_iter) {
       RK_TRY(apply_A(p, Ap));
-      double pAp;
+      double pAp = 0.0;
       RK_TRY(dot(p, Ap, &pAp));
       if (!(pAp > 0.0) || !std::isfinite(pAp)) return fail(RK_ERR_BREAKDOWN, "CG breakdown in the implicit step");
       const double al = rr / pAp;
       RK_CK(launch_axpby(x, al, p, 1.0, n, s));
       RK_CK(launch_axpby(r, -al, Ap, 1.0, n, s));
-      double rr2;
+      double rr2 = 0.0;
       RK_TRY(dot(r, r, &rr2));
       RK_CK(launch_axpby(p, 1.0, r, rr2 / rr, n, s));
       rr = rr2;
@@ -1583,7 +1583,7 @@ rk_status transient_implicit(rk_handle* h, const double* f, const double* g, dou
     // true residual of the step
     RK_TRY(apply_A(x, Ap));
     RK_CK(launch_sub(t, b, Ap, n, s));
-    double tr;
+    double tr = 0.0;
     RK_TRY(dot(t, t, &tr));
     info->rel_residual = std::max(info->rel_residual, std::sqrt(tr) / bn);
     if (!(std::sqrt(tr) <= 10.0 * o.tol * bn)) return fail(RK_ERR_NOT_CONVERGED, "implicit step not converged");
@@ -1653,28 +1653,28 @@ rk_status solve_penalty(rk_handle* h, const double* r, const double* g, const do
   RK_TRY(op_UT<double>(h, r, b, h->chiV64, nullptr, s));  // f^r (Alg. 4)
   RK_TRY(op_UT<double>(h, g, t, A, nullptr, s));          // U^T (A o g)
   RK_CK(launch_axpby(b, beta, t, 1.0, n, s));
-  double bn;
+  double bn = 0.0;
   RK_TRY(norm2(h, b, &bn, s));
   info->f_norm = bn;
   if (!std::isfinite(bn)) return fail(RK_ERR_INVALID_ARG, "right-hand side is not finite");
   RK_CK(launch_fill<double>(x, 0.0, n, s));
   RK_CK(launch_copy<double>(res, b, n, s));
   RK_CK(launch_copy<double>(p, b, n, s));
-  double rr;
+  double rr = 0.0;
   RK_CK(launch_dot<double, double>(res, res, n, h->partials, h->dscal, s));
   RK_TRY(read_scalar(h, h->dscal, &rr, s));
   const double target = o.tol * bn;
   int it = 0;
   while (std::sqrt(rr) > target && it < o.max_iter) {
     RK_TRY(apply(p, Ap));
-    double pAp;
+    double pAp = 0.0;
     RK_CK(launch_dot<double, double>(p, Ap, n, h->partials, h->dscal, s));
     RK_TRY(read_scalar(h, h->dscal, &pAp, s));
     if (!(pAp > 0.0) || !std::isfinite(pAp)) return fail(RK_ERR_BREAKDOWN, "penalty CG: p.Ap <= 0");
     const double alpha = rr / pAp;
     RK_CK(launch_axpby(x, alpha, p, 1.0, n, s));
     RK_CK(launch_axpby(res, -alpha, Ap, 1.0, n, s));
-    double rr_new;
+    double rr_new = 0.0;
     RK_CK(launch_dot<double, double>(res, res, n, h->partials, h->dscal, s));
     RK_TRY(read_scalar(h, h->dscal, &rr_new, s));
     RK_CK(launch_axpby(p, 1.0, res, rr_new / rr, n, s));
@@ -1748,7 +1748,7 @@ rk_status solve_nonlinear(rk_handle* h, const double* r, const double* g, int ki
   RK_TRY(op_K<double>(h, dG, Kx, h->chi, h->chi_omega, s));
   info->matvec_f64 += 1;
   RK_TRY(gradient(R));
-  double rr0, rr;
+  double rr0 = 0.0, rr = 0.0;
   RK_TRY(dot(R, R, &rr0));
   rr = rr0;
   info->f_norm = std::sqrt(rr0);
@@ -1759,14 +1759,14 @@ rk_status solve_nonlinear(rk_handle* h, const double* r, const double* g, int ki
     RK_TRY(op_K<double>(h, p, Kp, h->chi_omega, h->chi_omega, s));
     RK_TRY(op_U<double>(h, p, w, s));
     info->matvec_f64 += 1;
-    double pKp, pKx, pF;
+    double pKp = 0.0, pKx = 0.0, pF = 0.0;
     RK_TRY(dot(p, Kp, &pKp));
     RK_TRY(dot(p, Kx, &pKx));
     RK_TRY(dot(p, F, &pF));
     const double c0 = pKx - pF;
     double alpha = 0.0;
     for (int k = 0; k < 40; ++k) {
-      double s0, s1;
+      double s0 = 0.0, s1 = 0.0;
       RK_TRY(line(alpha, &s0, &s1));
       const double d1 = c0 + alpha * pKp + s0, d2 = pKp + s1;
       if (!(d2 > 0.0) || !std::isfinite(d1)) return fail(RK_ERR_BREAKDOWN, "nonlinear CG: line search failed");
@@ -2119,7 +2119,7 @@ rk_status prepare_mixed_job(rk_handle* h, const double* r, const double* g, cons
   info->matvec_f64++;
   RK_CK(launch_masked_diff(F, t0, F, h->chi_omega, n, s));
   RK_CK(launch_fill<double>(x, 0.0, n, s));
-  double fn;
+  double fn = 0.0;
   RK_TRY(norm2(h, F, &fn, s));
   info->f_norm = fn;
   if (!std::isfinite(fn))
